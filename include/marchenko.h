@@ -1,0 +1,219 @@
+/*
+ * marchenko.h - C ABI of the GB300 iterative Marchenko synthesis library.
+ *
+ * The library runs the hot loop of iterative Marchenko redatuming on one GPU:
+ * per Neumann iteration the synthesis of Eq. (1),
+ *     N_i(x_R, x_F, -t) = theta_t * integral_x integral_t' R(x_R, x, t - t') N_{i-1}(x, x_F, t') dt' dx,
+ * done in the frequency domain (Theory section: the time convolution is a
+ * per-frequency product, the space integral a sum over surface positions),
+ * followed by the time reversal and sign flip, the theta mute and the
+ * accumulation of f1+, f1-, f2 and p- (Algorithm 1, both loops fused into
+ * one pass per iteration).  Every step runs in this library's CUDA kernels.
+ *
+ * Conventions (shared by every entry point):
+ *  - sources and receivers coincide: nsrc == nrec == n positions x_i = i*dx;
+ *  - circular time grid of nt samples (nt a power of two, 32..8192); sample j
+ *    has signed time j*dt for j < nt/2 and (j - nt)*dt otherwise;
+ *    X(-t)[j] = X[(nt - j) mod nt];
+ *  - forward DFT unnormalised (kernel e^{-2 pi i jm/nt}), inverse 1/nt;
+ *  - kept band m = 0 .. n_w-1 with n_w = min(nt/2, floor(fmax_hz * nt * dt)) + 1
+ *    (FP64, evaluated left to right); fmax_hz <= 0 keeps the full band; bins
+ *    outside the band are zero before every inverse transform, and the
+ *    imaginary parts of the DC and Nyquist bins do not enter a real trace;
+ *  - synthesis scale c = dx * dt (Riemann sums of both integrals):
+ *        S_m(k, f) = c * sum_r R_m(k, r) * N_m(r, f),  s = IDFT(S);
+ *  - N_i = -theta * s(-t) (Algorithm 1: time-reverse, multiply by -1, mute);
+ *    theta_k(j) = 1 iff |t_j| < t_d(f, x_k) - eps (FP64 comparison
+ *    j*dt < t_d - eps, exactly as written), symmetric in +-t;
+ *  - accumulation per iteration index i (0-based, Algorithm 1):
+ *        pmin += s;  f2p += N_i;  i even: f1min -= N_i(-t);  i odd: f1plus += N_i;
+ *    initial values N_{-1} = f1plus = f2p = G_d(-t), f1min = pmin = 0;
+ *  - G(t) = f2p(-t) + pmin(t).
+ *
+ * Layouts (row-major, last index fastest):
+ *  - R band spectra passed to mk_load_R: complex64 (float re, float im)
+ *    [w_count][nsrc][nrec], R[m][k][r] = R(x_R = x_k, x = x_r, f_m); the
+ *    contraction sums over the last (receiver) axis, which by reciprocity
+ *    R(x_k, x_r) = R(x_r, x_k) is the space integral of Eq. (1);
+ *  - G_d: float [nfocal][nrec][nt], the first arrival G_d(x_r, x_F, t);
+ *  - t_d: double [nfocal][nrec], first-arrival times in seconds;
+ *  - every field: float [nfocal][nsrc][nt].
+ *
+ * Memory and ownership:
+ *  - the plan allocates no device memory: the caller passes one device
+ *    workspace of at least mk_workspace_size() bytes (256-byte aligned) to
+ *    mk_plan and keeps it alive until mk_destroy;
+ *  - input and output buffers belong to the caller and need to stay valid
+ *    only during the call (the library copies from and to them);
+ *  - all GPU work is issued on the stream given to mk_plan.  Calls that read
+ *    host memory or write host outputs return after that work is complete;
+ *    calls on device buffers only are asynchronous on the stream;
+ *  - a plan is not thread-safe: one host thread at a time per plan.
+ *
+ * Errors: every entry point returns mk_status and never aborts.  The message
+ * of the last failure is returned by mk_last_error(plan) (plan may be NULL
+ * for failures that happen before a plan exists); the string stays valid
+ * until the next call on the same plan (or on any NULL-plan call).
+ */
+#ifndef MARCHENKO_H
+#define MARCHENKO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mk_plan_s* mk_plan_t;
+
+typedef enum {
+  MK_OK = 0,
+  MK_ERR_ARG = 1,          /* invalid argument (null pointer, size, index)   */
+  MK_ERR_STATE = 2,        /* call out of order (e.g. iterate before G_d)    */
+  MK_ERR_OOM = 3,          /* workspace too small                            */
+  MK_ERR_CUDA = 4,         /* a CUDA runtime call failed                     */
+  MK_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out             */
+  MK_ERR_UNSUPPORTED = 6   /* valid request this build does not implement    */
+} mk_status;
+
+/* Storage precision of R in the workspace. */
+typedef enum {
+  MK_R_C64 = 0,        /* complex FP32                                        */
+  MK_R_CBF16 = 1,      /* complex BF16 (tensor-core contraction)              */
+  MK_R_CF16 = 2,       /* complex FP16 (tensor-core contraction)              */
+  MK_R_SPLIT_BF16 = 3  /* BF16 hi + BF16 lo parts (3-product tensor-core form) */
+} mk_rprec;
+
+/* Field selection bits for mk_fetch_fields (output order = bit order). */
+#define MK_F_N    (1u << 0) /* the last N_i (N_{-1} before any iteration)  */
+#define MK_F_F1P  (1u << 1) /* f1plus                                      */
+#define MK_F_F1M  (1u << 2) /* f1min                                       */
+#define MK_F_F2P  (1u << 3) /* f2p                                         */
+#define MK_F_PMIN (1u << 4) /* pmin                                        */
+#define MK_F_G    (1u << 5) /* G = f2p(-t) + pmin(t)                       */
+#define MK_F_ALL  (0x3Fu)
+
+/* mk_desc.flags */
+#define MK_FLAG_TIMING (1u << 0) /* record CUDA events around every kernel   */
+
+/* One survey.  nsrc == nrec is required (coincident sources/receivers). */
+typedef struct {
+  int32_t nsrc;     /* number of output positions k                          */
+  int32_t nrec;     /* number of summed positions r                          */
+  int32_t nt;       /* time samples, power of two in [32, 8192]               */
+  int32_t nfocal;   /* focal points F >= 1                                    */
+  double dt;        /* sample interval, s (> 0)                               */
+  double dx;        /* position spacing, m (> 0)                              */
+  double fmax_hz;   /* band limit (<= 0: full band)                           */
+  int32_t rprec;    /* mk_rprec                                               */
+  uint32_t flags;   /* MK_FLAG_*                                              */
+} mk_desc;
+
+/* Counters of one plan (mk_get_stats). */
+typedef struct {
+  uint64_t launches;           /* kernels this plan launched                  */
+  uint64_t contract_launches;  /* contraction launches (Eq. 1 space integral) */
+  uint64_t epilogue_launches;  /* IFFT/mute/accumulate/FFT launches           */
+  uint64_t other_launches;     /* init, G and conversion launches             */
+  double contract_ms;          /* summed event time (MK_FLAG_TIMING only)     */
+  double epilogue_ms;          /* summed event time (MK_FLAG_TIMING only)     */
+  uint64_t contract_timed;     /* launches included in contract_ms            */
+  uint64_t epilogue_timed;     /* launches included in epilogue_ms            */
+} mk_stats_t;
+
+/*
+ * mk_workspace_size - device bytes a plan for these surveys needs.
+ *   d, ndesc: ndesc >= 1 survey descriptions (validated as in mk_plan).
+ *   bytes:    out, the size to allocate.
+ * Errors: MK_ERR_ARG (null pointer, invalid description), MK_ERR_UNSUPPORTED.
+ */
+mk_status mk_workspace_size(const mk_desc* d, int32_t ndesc, size_t* bytes);
+
+/*
+ * mk_plan - create a plan for ndesc independent surveys (Algorithm 1, one
+ * Neumann series per survey and focal point).
+ *   cuda_stream: cudaStream_t the plan issues all its work on (NULL: legacy
+ *                default stream).  The current device at this call is the
+ *                plan's device; later calls must be made with it current.
+ *   workspace:   device pointer, 256-byte aligned, >= mk_workspace_size bytes;
+ *                zeroed and carved by the plan, owned by the caller.
+ *   out:         receives the plan handle.
+ * Errors: MK_ERR_ARG, MK_ERR_OOM (workspace_bytes too small),
+ *         MK_ERR_UNSUPPORTED, MK_ERR_CUDA.
+ */
+mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* workspace,
+                  size_t workspace_bytes, mk_plan_t* out);
+
+/*
+ * mk_load_R - load band spectra R_m for bins w_begin .. w_begin+w_count-1 of
+ * one survey (Implementation section: the reflection data is read, Fourier
+ * transformed and kept resident; here it is resident in HBM in the plan's
+ * storage precision, rows padded for aligned loads).
+ *   Rw: complex64 [w_count][nsrc][nrec] on the host (src_on_device = 0) or
+ *       on the device (src_on_device = 1).
+ * Loading may be done in chunks of bins, in any order; mk_set_Gd_window
+ * requires every bin 0 .. n_w-1 to have been loaded.
+ * Errors: MK_ERR_ARG (bad survey index or bin range), MK_ERR_CUDA.
+ */
+mk_status mk_load_R(mk_plan_t plan, int32_t survey, const void* Rw, int32_t w_begin,
+                    int32_t w_count, int32_t src_on_device);
+
+/*
+ * mk_set_Gd_window - start the Neumann series of one survey (Theory:
+ * initialisation N_{-1} = f1+_0 = G_d(-t)): sets N_{-1} = f1plus = f2p =
+ * G_d(-t), f1min = pmin = 0, the mute windows from t_d and eps, and the band
+ * spectrum of N_{-1}; resets the iteration index to 0.
+ *   Gd: float [nfocal][nrec][nt]; td: double [nfocal][nrec] (seconds); both
+ *       on the host (src_on_device = 0) or both on the device (1).
+ *   eps_s: window shift in seconds (theta keeps |t| < t_d - eps_s).
+ * Errors: MK_ERR_ARG, MK_ERR_STATE (R not fully loaded), MK_ERR_CUDA.
+ */
+mk_status mk_set_Gd_window(mk_plan_t plan, int32_t survey, const float* Gd, const double* td,
+                           double eps_s, int32_t src_on_device);
+
+/*
+ * mk_iterate - run niter Neumann iterations of every survey, continuing the
+ * series from where it stopped (Algorithm 1, loop over iter; one synthesis,
+ * reversal, mute and accumulation per iteration).
+ *   energy: NULL, or host double [niter][sum of nfocal over surveys]:
+ *           E_i(f) = sum over (k, t) of N_i^2, accumulated in FP64 in a fixed
+ *           order (deterministic).  With energy != NULL the call returns
+ *           after the work is done; with NULL it is asynchronous.
+ * Errors: MK_ERR_ARG (niter < 0), MK_ERR_STATE (a survey without G_d),
+ *         MK_ERR_CUDA.
+ */
+mk_status mk_iterate(mk_plan_t plan, int32_t niter, double* energy);
+
+/*
+ * mk_fetch_fields - copy selected fields of one survey out, in bit order of
+ * mask, each float [nfocal][nsrc][nt] (MK_F_G is computed on the GPU).
+ *   out: host (dst_on_device = 0) or device (1) buffer of out_bytes >=
+ *        popcount(mask) * nfocal * nsrc * nt * 4.
+ * Errors: MK_ERR_ARG, MK_ERR_STATE (G_d not set), MK_ERR_CUDA.
+ */
+mk_status mk_fetch_fields(mk_plan_t plan, int32_t survey, uint32_t mask, float* out,
+                          size_t out_bytes, int32_t dst_on_device);
+
+/*
+ * mk_get_stats - launch counters and (with MK_FLAG_TIMING on every survey's
+ * description) summed CUDA-event times of the contraction and epilogue
+ * kernels, measured on the plan's stream.  Synchronises the stream.
+ *   reset != 0 zeroes the counters after reading them.
+ * Errors: MK_ERR_ARG, MK_ERR_CUDA.
+ */
+mk_status mk_get_stats(mk_plan_t plan, mk_stats_t* out, int32_t reset);
+
+/* mk_destroy - release the plan's host state (not the caller's workspace).
+ * Synchronises the plan's stream.  NULL is accepted. */
+mk_status mk_destroy(mk_plan_t plan);
+
+/* mk_last_error - message of the last failed call on plan (NULL: of the last
+ * failed call made without a plan); "" when none. */
+const char* mk_last_error(mk_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MARCHENKO_H */

@@ -1,0 +1,123 @@
+"""PyTorch-facing wrapper of the C ABI.
+
+PyTorch provides the device workspace (one uint8 tensor from its caching
+allocator) and the CUDA stream; every computation runs in libmarchenko.so.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _native as N
+from . import binding as B
+
+
+@dataclass
+class Desc:
+    """Mirror of the C ``mk_desc`` (one survey)."""
+
+    nsrc: int
+    nrec: int
+    nt: int
+    nfocal: int
+    dt: float
+    dx: float
+    fmax_hz: float = 0.0
+    rprec: int = N.MK_R_C64
+    flags: int = 0
+
+    @property
+    def nw(self) -> int:
+        if not self.fmax_hz > 0:
+            return self.nt // 2 + 1
+        return min(self.nt // 2, int(np.floor(self.fmax_hz * self.nt * self.dt))) + 1
+
+
+def _ptr_host(a: np.ndarray, dtype) -> tuple[np.ndarray, int]:
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data
+
+
+class Plan:
+    """A plan over one or more surveys on one CUDA device.
+
+    Inputs may be NumPy arrays (host) or CUDA tensors (device); outputs are
+    NumPy arrays unless a CUDA tensor ``out`` is given.
+    """
+
+    def __init__(self, descs, device=None, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: libmarchenko has no CPU path")
+        self.descs = list(descs)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = B.mk_workspace_size(self.descs)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+            self.handle = B.mk_plan(self.descs, self.stream.cuda_stream, self.workspace.data_ptr(), nbytes)
+        self.workspace_bytes = nbytes
+
+    # -- inputs ---------------------------------------------------------------
+    def load_R(self, survey: int, Rw, w_begin: int = 0) -> None:
+        """Band spectra R[m][k][r] (complex64) for bins w_begin .. w_begin + len - 1."""
+        if isinstance(Rw, torch.Tensor):
+            assert Rw.is_cuda and Rw.dtype == torch.complex64 and Rw.is_contiguous()
+            B.mk_load_R(self.handle, survey, Rw.data_ptr(), w_begin, Rw.shape[0], True)
+        else:
+            a, p = _ptr_host(Rw, np.complex64)
+            B.mk_load_R(self.handle, survey, p, w_begin, a.shape[0], False)
+
+    def set_Gd_window(self, survey: int, Gd, td, eps: float) -> None:
+        """First arrivals G_d [F][n][nt] (float32) and t_d [F][n] (float64, s)."""
+        if isinstance(Gd, torch.Tensor):
+            assert Gd.is_cuda and isinstance(td, torch.Tensor) and td.is_cuda
+            Gd = Gd.contiguous().to(torch.float32)
+            td = td.contiguous().to(torch.float64)
+            B.mk_set_Gd_window(self.handle, survey, Gd.data_ptr(), td.data_ptr(), float(eps), True)
+        else:
+            g, gp = _ptr_host(Gd, np.float32)
+            t, tp = _ptr_host(td, np.float64)
+            B.mk_set_Gd_window(self.handle, survey, gp, tp, float(eps), False)
+
+    # -- iterations -----------------------------------------------------------
+    def iterate(self, niter: int, energy: bool = True):
+        """Run niter Neumann iterations; returns energies [niter][sum F] or None."""
+        if not energy:
+            B.mk_iterate(self.handle, niter, None)
+            return None
+        ftot = sum(d.nfocal for d in self.descs)
+        e = np.zeros((niter, ftot), dtype=np.float64)
+        B.mk_iterate(self.handle, niter, e.ctypes.data if niter else None)
+        return e
+
+    # -- outputs --------------------------------------------------------------
+    def fetch_fields(self, survey: int, mask: int = N.MK_F_ALL, out=None):
+        d = self.descs[survey]
+        nf = bin(mask).count("1")
+        shape = (nf, d.nfocal, d.nsrc, d.nt)
+        if out is None:
+            out = np.empty(shape, dtype=np.float32)
+        if isinstance(out, torch.Tensor):
+            assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+            B.mk_fetch_fields(self.handle, survey, mask, out.data_ptr(), out.numel() * 4, True)
+        else:
+            assert out.dtype == np.float32 and out.flags.c_contiguous
+            B.mk_fetch_fields(self.handle, survey, mask, out.ctypes.data, out.nbytes, False)
+        return out
+
+    def stats(self, reset: bool = False) -> dict:
+        return B.mk_get_stats(self.handle, reset)
+
+    def close(self) -> None:
+        if getattr(self, "handle", 0):
+            B.mk_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,440 @@
+// Host side of the C ABI declared in include/marchenko.h: argument checks,
+// workspace carving, call-order state, launches and error reporting.
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/marchenko.h"
+#include "mk_internal.h"
+
+namespace {
+
+constexpr int kMaxIterSlots = 256;  // energies buffered on the device per chunk of iterations
+constexpr size_t kAlign = 256;
+
+thread_local char g_noplan_err[512] = "";
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Survey {
+  mk_desc d;
+  mk::SurveyDev dev;
+  double* energy = nullptr;  // [kMaxIterSlots][F] device
+  std::vector<unsigned char> loaded;
+  int nloaded = 0;
+  bool ready = false;
+  int iter = 0;
+  size_t offset = 0, bytes = 0;  // carving inside the workspace
+};
+
+struct TimedPair {
+  cudaEvent_t a, b;
+  int kind;  // 0 contraction, 1 epilogue
+};
+
+}  // namespace
+
+struct mk_plan_s {
+  std::vector<Survey> s;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 1;
+  bool timing = false;
+  char err[512] = "";
+  mk_stats_t stats{};
+  std::vector<TimedPair> events;  // created once, reused
+  size_t next_event = 0;
+};
+
+namespace {
+
+mk_status fail(mk_plan_t p, mk_status st, const char* fmt, ...) {
+  char* buf = p ? p->err : g_noplan_err;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define MK_CUDA(p, call)                                                                    \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail((p), MK_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                      \
+  } while (0)
+
+int band_bins(const mk_desc& d) {
+  if (!(d.fmax_hz > 0.0)) return d.nt / 2 + 1;
+  const double q = floor(d.fmax_hz * d.nt * d.dt);
+  const int half = d.nt / 2;
+  return (q >= half ? half : (int)q) + 1;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
+  if (d.nsrc < 1 || d.nrec < 1 || d.nfocal < 1)
+    return fail(p, MK_ERR_ARG, "survey %d: nsrc, nrec and nfocal must be >= 1", i);
+  if (d.nsrc != d.nrec)
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nsrc (%d) != nrec (%d); coincident positions required",
+                i, d.nsrc, d.nrec);
+  if (!is_pow2(d.nt) || d.nt < 32 || d.nt > 8192)
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nt=%d must be a power of two in [32, 8192]", i, d.nt);
+  if (!(d.dt > 0.0) || !(d.dx > 0.0) || !isfinite(d.dt) || !isfinite(d.dx))
+    return fail(p, MK_ERR_ARG, "survey %d: dt and dx must be finite and > 0", i);
+  if (d.rprec != MK_R_C64)
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: R storage precision %d not available in this build", i,
+                d.rprec);
+  if ((int64_t)d.nsrc * d.nfocal > (int64_t)1 << 30)
+    return fail(p, MK_ERR_ARG, "survey %d: nsrc * nfocal too large", i);
+  return MK_OK;
+}
+
+// Sizes and strides of one survey; carves the workspace when base != nullptr.
+size_t layout(Survey& sv, char* base) {
+  const mk_desc& d = sv.d;
+  mk::SurveyDev& v = sv.dev;
+  v.ns = d.nsrc;
+  v.nt = d.nt;
+  v.F = d.nfocal;
+  v.nw = band_bins(d);
+  v.r_pad = (d.nrec + 31) / 32 * 32;
+  v.ncols = v.ns * v.F;
+  v.s_stride = ((int64_t)v.ncols + 1 + 3) / 4 * 4;
+  v.nw_stride = (int64_t)v.r_pad * v.F;
+  v.dt = d.dt;
+  v.c = (float)(d.dx * d.dt);
+  v.inv_nt = 1.0f / (float)d.nt;
+  v.rprec = d.rprec;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* ptr = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return ptr;
+  };
+  const size_t field = (size_t)v.F * v.ns * v.nt * sizeof(float);
+  v.R = reinterpret_cast<const float2*>(take((size_t)v.nw * v.ns * v.r_pad * sizeof(float2)));
+  v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
+  v.S = reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)));
+  v.fN = reinterpret_cast<float*>(take(field));
+  v.f1p = reinterpret_cast<float*>(take(field));
+  v.f1m = reinterpret_cast<float*>(take(field));
+  v.f2p = reinterpret_cast<float*>(take(field));
+  v.pmin = reinterpret_cast<float*>(take(field));
+  v.scratch = reinterpret_cast<float*>(take(field));
+  v.L = reinterpret_cast<int*>(take((size_t)(v.ncols + 1) * sizeof(int)));
+  v.td = reinterpret_cast<double*>(take((size_t)v.ncols * sizeof(double)));
+  v.Epart = reinterpret_cast<double*>(take((size_t)(v.ncols + 1) * sizeof(double)));
+  v.counter = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
+  v.tw = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));
+  sv.energy = reinterpret_cast<double*>(take((size_t)kMaxIterSlots * v.F * sizeof(double)));
+  return off;
+}
+
+mk_status get_survey(mk_plan_t p, int32_t survey, Survey** out) {
+  if (!p) return fail(nullptr, MK_ERR_ARG, "null plan");
+  if (survey < 0 || survey >= (int32_t)p->s.size())
+    return fail(p, MK_ERR_ARG, "survey index %d out of range [0, %d)", survey, (int)p->s.size());
+  *out = &p->s[survey];
+  return MK_OK;
+}
+
+mk_status ensure_device(mk_plan_t p) {
+  int dev = -1;
+  MK_CUDA(p, cudaGetDevice(&dev));
+  if (dev != p->device)
+    return fail(p, MK_ERR_STATE, "current device %d is not the plan's device %d", dev, p->device);
+  return MK_OK;
+}
+
+TimedPair* next_pair(mk_plan_t p, int kind) {
+  if (!p->timing) return nullptr;
+  if (p->next_event == p->events.size()) {
+    TimedPair tp;
+    if (cudaEventCreate(&tp.a) != cudaSuccess) return nullptr;
+    if (cudaEventCreate(&tp.b) != cudaSuccess) {
+      cudaEventDestroy(tp.a);
+      return nullptr;
+    }
+    p->events.push_back(tp);
+  }
+  TimedPair* tp = &p->events[p->next_event++];
+  tp->kind = kind;
+  return tp;
+}
+
+}  // namespace
+
+extern "C" {
+
+mk_status mk_workspace_size(const mk_desc* d, int32_t ndesc, size_t* bytes) {
+  g_noplan_err[0] = 0;
+  if (!d || !bytes || ndesc < 1) return fail(nullptr, MK_ERR_ARG, "null pointer or ndesc < 1");
+  size_t total = 0;
+  for (int i = 0; i < ndesc; ++i) {
+    mk_status st = check_desc(nullptr, d[i], i);
+    if (st != MK_OK) return st;
+    Survey sv;
+    sv.d = d[i];
+    total += layout(sv, nullptr);
+  }
+  *bytes = total;
+  return MK_OK;
+}
+
+mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* workspace,
+                  size_t workspace_bytes, mk_plan_t* out) {
+  g_noplan_err[0] = 0;
+  if (!d || !out || ndesc < 1 || !workspace) return fail(nullptr, MK_ERR_ARG, "null pointer or ndesc < 1");
+  *out = nullptr;
+  if (((uintptr_t)workspace) % kAlign != 0) return fail(nullptr, MK_ERR_ARG, "workspace not 256-byte aligned");
+  size_t need = 0;
+  mk_status st = mk_workspace_size(d, ndesc, &need);
+  if (st != MK_OK) return st;
+  if (workspace_bytes < need)
+    return fail(nullptr, MK_ERR_OOM, "workspace of %zu bytes is smaller than the %zu needed", workspace_bytes,
+                need);
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, workspace);
+  if (e != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return fail(nullptr, MK_ERR_ARG, "workspace is not device memory");
+  }
+  mk_plan_t p = new (std::nothrow) mk_plan_s();
+  if (!p) return fail(nullptr, MK_ERR_OOM, "host allocation of the plan failed");
+  p->stream = static_cast<cudaStream_t>(cuda_stream);
+  p->device = attr.device;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != attr.device) {
+    delete p;
+    return fail(nullptr, MK_ERR_ARG, "workspace belongs to device %d, current device is %d", attr.device, cur);
+  }
+  if ((e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, cur)) != cudaSuccess ||
+      (e = mk::prepare_kernels()) != cudaSuccess) {
+    delete p;
+    return fail(nullptr, MK_ERR_CUDA, "device setup failed: %s", cudaGetErrorString(e));
+  }
+  p->s.resize(ndesc);
+  size_t off = 0;
+  char* base = static_cast<char*>(workspace);
+  bool timing = true;
+  for (int i = 0; i < ndesc; ++i) {
+    Survey& sv = p->s[i];
+    sv.d = d[i];
+    sv.offset = off;
+    sv.bytes = layout(sv, base + off);
+    off += sv.bytes;
+    sv.loaded.assign(sv.dev.nw, 0);
+    timing = timing && (d[i].flags & MK_FLAG_TIMING);
+  }
+  p->timing = timing;
+  // Zero the workspace (padding of R and Nw must be zero), then the twiddles.
+  if ((e = cudaMemsetAsync(workspace, 0, off, p->stream)) != cudaSuccess) {
+    delete p;
+    return fail(nullptr, MK_ERR_CUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+  }
+  for (auto& sv : p->s) {
+    const int nt = sv.dev.nt;
+    std::vector<float2> tw(nt);
+    for (int q = 0; q < nt; ++q) {
+      const double a = -2.0 * M_PI * (double)q / (double)nt;
+      tw[q] = make_float2((float)cos(a), (float)sin(a));
+    }
+    e = cudaMemcpyAsync(const_cast<float2*>(sv.dev.tw), tw.data(), nt * sizeof(float2), cudaMemcpyHostToDevice,
+                        p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+      delete p;
+      return fail(nullptr, MK_ERR_CUDA, "twiddle upload failed: %s", cudaGetErrorString(e));
+    }
+  }
+  *out = p;
+  return MK_OK;
+}
+
+mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin, int32_t w_count,
+                    int32_t src_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  const mk::SurveyDev& v = sv->dev;
+  if (!Rw) return fail(p, MK_ERR_ARG, "null R pointer");
+  if (w_begin < 0 || w_count < 0 || w_begin + w_count > v.nw)
+    return fail(p, MK_ERR_ARG, "bins [%d, %d) outside the band [0, %d)", w_begin, w_begin + w_count, v.nw);
+  if (w_count == 0) return MK_OK;
+  float2* dst = const_cast<float2*>(v.R) + (size_t)w_begin * v.ns * v.r_pad;
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  MK_CUDA(p, cudaMemcpy2DAsync(dst, (size_t)v.r_pad * sizeof(float2), Rw, (size_t)v.ns * sizeof(float2),
+                               (size_t)v.ns * sizeof(float2), (size_t)w_count * v.ns, kind, p->stream));
+  if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  for (int m = w_begin; m < w_begin + w_count; ++m) {
+    if (!sv->loaded[m]) {
+      sv->loaded[m] = 1;
+      ++sv->nloaded;
+    }
+  }
+  return MK_OK;
+}
+
+mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const double* td, double eps_s,
+                           int32_t src_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!Gd || !td) return fail(p, MK_ERR_ARG, "null G_d or t_d pointer");
+  if (!isfinite(eps_s)) return fail(p, MK_ERR_ARG, "eps must be finite");
+  mk::SurveyDev& v = sv->dev;
+  if (sv->nloaded != v.nw)
+    return fail(p, MK_ERR_STATE, "R of survey %d has %d of %d bins loaded", survey, sv->nloaded, v.nw);
+  // windows from t_d, then N_{-1}, accumulators and the spectrum of N_{-1}
+  const double* tsrc = td;
+  const float* gsrc = Gd;
+  if (!src_on_device) {
+    MK_CUDA(p, cudaMemcpyAsync(v.td, td, (size_t)v.F * v.ns * sizeof(double), cudaMemcpyHostToDevice,
+                               p->stream));
+    MK_CUDA(p, cudaMemcpyAsync(v.scratch, Gd, (size_t)v.F * v.ns * v.nt * sizeof(float),
+                               cudaMemcpyHostToDevice, p->stream));
+    tsrc = v.td;
+    gsrc = v.scratch;
+  }
+  MK_CUDA(p, mk::launch_windows(v, tsrc, eps_s, p->stream));
+  MK_CUDA(p, mk::launch_init(v, gsrc, p->stream, p->num_sms));
+  p->stats.launches += 2;
+  p->stats.other_launches += 2;
+  if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  sv->ready = true;
+  sv->iter = 0;
+  return MK_OK;
+}
+
+mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
+  if (!p) return fail(nullptr, MK_ERR_ARG, "null plan");
+  p->err[0] = 0;
+  mk_status st = ensure_device(p);
+  if (st != MK_OK) return st;
+  if (niter < 0) return fail(p, MK_ERR_ARG, "niter < 0");
+  int Ftot = 0;
+  for (size_t i = 0; i < p->s.size(); ++i) {
+    if (!p->s[i].ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", (int)i);
+    Ftot += p->s[i].dev.F;
+  }
+  for (int done = 0; done < niter;) {
+    const int chunk = niter - done < kMaxIterSlots ? niter - done : kMaxIterSlots;
+    for (int it = 0; it < chunk; ++it) {
+      for (auto& sv : p->s) {
+        TimedPair* tp = next_pair(p, 0);
+        if (tp) MK_CUDA(p, cudaEventRecord(tp->a, p->stream));
+        int nl = 0;
+        MK_CUDA(p, mk::launch_contract(sv.dev, p->stream, p->num_sms, &nl));
+        if (tp) MK_CUDA(p, cudaEventRecord(tp->b, p->stream));
+        p->stats.launches += nl;
+        p->stats.contract_launches += nl;
+        tp = next_pair(p, 1);
+        if (tp) MK_CUDA(p, cudaEventRecord(tp->a, p->stream));
+        MK_CUDA(p, mk::launch_epilogue(sv.dev, sv.iter & 1, sv.energy + (size_t)it * sv.dev.F, p->stream,
+                                       p->num_sms));
+        if (tp) MK_CUDA(p, cudaEventRecord(tp->b, p->stream));
+        p->stats.launches++;
+        p->stats.epilogue_launches++;
+        sv.iter++;
+      }
+    }
+    if (energy) {
+      int foff = 0;
+      for (auto& sv : p->s) {
+        MK_CUDA(p, cudaMemcpy2DAsync(energy + (size_t)done * Ftot + foff, (size_t)Ftot * sizeof(double),
+                                     sv.energy, (size_t)sv.dev.F * sizeof(double),
+                                     (size_t)sv.dev.F * sizeof(double), chunk, cudaMemcpyDeviceToHost,
+                                     p->stream));
+        foff += sv.dev.F;
+      }
+      MK_CUDA(p, cudaStreamSynchronize(p->stream));
+    }
+    done += chunk;
+  }
+  return MK_OK;
+}
+
+mk_status mk_fetch_fields(mk_plan_t p, int32_t survey, uint32_t mask, float* out, size_t out_bytes,
+                          int32_t dst_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!out) return fail(p, MK_ERR_ARG, "null output pointer");
+  if (mask == 0 || (mask & ~MK_F_ALL)) return fail(p, MK_ERR_ARG, "field mask 0x%x invalid", mask);
+  if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
+  const mk::SurveyDev& v = sv->dev;
+  const size_t field = (size_t)v.F * v.ns * v.nt;
+  const size_t need = (size_t)__builtin_popcount(mask) * field * sizeof(float);
+  if (out_bytes < need) return fail(p, MK_ERR_ARG, "output of %zu bytes, %zu needed", out_bytes, need);
+  const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const float* src[6] = {v.fN, v.f1p, v.f1m, v.f2p, v.pmin, nullptr};
+  float* o = out;
+  for (int b = 0; b < 6; ++b) {
+    if (!(mask & (1u << b))) continue;
+    if (b == 5) {
+      float* gdst = dst_on_device ? o : v.scratch;
+      MK_CUDA(p, mk::launch_green(v, gdst, p->stream, p->num_sms));
+      p->stats.launches++;
+      p->stats.other_launches++;
+      if (!dst_on_device)
+        MK_CUDA(p, cudaMemcpyAsync(o, v.scratch, field * sizeof(float), cudaMemcpyDeviceToHost, p->stream));
+    } else {
+      MK_CUDA(p, cudaMemcpyAsync(o, src[b], field * sizeof(float), kind, p->stream));
+    }
+    o += field;
+  }
+  if (!dst_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  return MK_OK;
+}
+
+mk_status mk_get_stats(mk_plan_t p, mk_stats_t* out, int32_t reset) {
+  if (!p || !out) return fail(p, MK_ERR_ARG, "null pointer");
+  p->err[0] = 0;
+  if (p->next_event) {
+    MK_CUDA(p, cudaStreamSynchronize(p->stream));
+    for (size_t i = 0; i < p->next_event; ++i) {
+      float ms = 0.f;
+      MK_CUDA(p, cudaEventElapsedTime(&ms, p->events[i].a, p->events[i].b));
+      if (p->events[i].kind == 0) {
+        p->stats.contract_ms += ms;
+        p->stats.contract_timed++;
+      } else {
+        p->stats.epilogue_ms += ms;
+        p->stats.epilogue_timed++;
+      }
+    }
+    p->next_event = 0;
+  }
+  *out = p->stats;
+  if (reset) p->stats = mk_stats_t{};
+  return MK_OK;
+}
+
+mk_status mk_destroy(mk_plan_t p) {
+  if (!p) return MK_OK;
+  cudaStreamSynchronize(p->stream);
+  for (auto& tp : p->events) {
+    cudaEventDestroy(tp.a);
+    cudaEventDestroy(tp.b);
+  }
+  delete p;
+  return MK_OK;
+}
+
+const char* mk_last_error(mk_plan_t p) { return p ? p->err : g_noplan_err; }
+
+}  // extern "C"

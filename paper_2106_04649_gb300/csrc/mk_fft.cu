@@ -1,0 +1,435 @@
+// Per-trace transforms of the Neumann iteration, staged in shared memory.
+//
+//  * epilogue: inverse transform of the band-limited synthesis result
+//    (Theory: "reverse Fourier transform"; Implementation: "padding"), time
+//    reversal and sign flip, theta mute, accumulation of pmin, f2p, f1min /
+//    f1plus (Algorithm 1), FP64 energy, and the forward transform of N_i
+//    restricted to the band for the next contraction;
+//  * init: N_{-1} = f1plus = f2p = G_d(-t), f1min = pmin = 0 and the band
+//    spectrum of N_{-1} (Theory: initialisation);
+//  * green: G(t) = f2p(-t) + pmin(t).
+//
+// Two real traces share one complex transform (a + i b): the inverse
+// transform of X + iY with Hermitian X, Y gives x + iy; the forward transform
+// Z of a + ib gives A_m = (Z_m + conj Z_{-m})/2, B_m = (Z_m - conj Z_{-m})/(2i).
+// The complex transform is a Stockham autosort FFT (radix 4, one radix-2
+// stage when log2 nt is odd) in shared memory with twiddles from an FP64 host
+// table rounded to FP32.  One CTA processes one pair of traces at a time and
+// loops over pairs (grid sized to the SM count).
+
+#include "mk_internal.h"
+
+namespace mk {
+namespace {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+
+// multiply by -i (forward transform) or +i (inverse transform)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 v) {
+  return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  float2 a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = mul_mi<INV>(csub(v1, v3));
+  v0 = cadd(a0, a2);
+  v2 = csub(a0, a2);
+  v1 = cadd(a1, a3);
+  v3 = csub(a1, a3);
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
+__host__ __device__ constexpr int threads_for(int nt) { return nt / 8 < 32 ? 32 : (nt / 8 > 512 ? 512 : nt / 8); }
+
+// In-place complex DFT of x[0..NT) (unnormalised; sign -1 forward, +1 inverse).
+// Stockham stage with current sub-length Ns and radix R: butterfly j
+// (k = j mod Ns) reads x[j + r NT/R], applies twiddles w^{r k NT/(Ns R)},
+// does a length-R DFT and writes x[(j - k) R + k + r Ns].  Reads and writes
+// of a stage are separated by a barrier, so the stage works in place.
+template <int NT, int THREADS, bool INV>
+__device__ __forceinline__ void fft_smem(float2* x, const float2* tw) {
+  constexpr int LOG2 = ilog2(NT);
+  constexpr int NB4 = NT / 4;
+  constexpr int P4 = (NB4 + THREADS - 1) / THREADS;
+  int Ns = 1;
+#pragma unroll 1
+  for (int s = 0; s < LOG2 / 2; ++s) {
+    float2 v[P4][4];
+    const int step = NT / (Ns * 4);
+#pragma unroll
+    for (int q = 0; q < P4; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      if (j < NB4) {
+        const int k = j & (Ns - 1);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[q][r] = x[j + r * NB4];
+#pragma unroll
+        for (int r = 1; r < 4; ++r) {
+          float2 w = tw[r * k * step];
+          if (INV) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
+        dft4<INV>(v[q][0], v[q][1], v[q][2], v[q][3]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < P4; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      if (j < NB4) {
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * 4 + k;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x[base + r * Ns] = v[q][r];
+      }
+    }
+    __syncthreads();
+    Ns *= 4;
+  }
+  if (LOG2 & 1) {
+    constexpr int NB2 = NT / 2;
+    constexpr int P2 = (NB2 + THREADS - 1) / THREADS;
+    float2 v[P2][2];
+#pragma unroll
+    for (int q = 0; q < P2; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      if (j < NB2) {
+        const int k = j & (Ns - 1);
+        v[q][0] = x[j];
+        float2 w = tw[k * (NT / (Ns * 2))];
+        if (INV) w.y = -w.y;
+        v[q][1] = cmul(x[j + NB2], w);
+        const float2 a = v[q][0];
+        v[q][0] = cadd(a, v[q][1]);
+        v[q][1] = csub(a, v[q][1]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < P2; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      if (j < NB2) {
+        const int k = j & (Ns - 1);
+        const int base = (j - k) * 2 + k;
+        x[base] = v[q][0];
+        x[base + Ns] = v[q][1];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Block-wide sum of two doubles in a fixed order (deterministic).
+template <int THREADS>
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  constexpr int NWARP = THREADS / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[2 * wid] = a;
+    red[2 * wid + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < NWARP; ++w) {
+      sa += red[2 * w];
+      sb += red[2 * w + 1];
+    }
+    a = sa;
+    b = sb;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int64_t field_offset(const SurveyDev& s, int t) {
+  const int f = t % s.F, k = t / s.F;
+  return ((int64_t)f * s.ns + k) * s.nt;
+}
+
+// Forward transform of the pair held in x (a + i b), unpacked into the band
+// spectra A_m, B_m for m < nw and written to Nw[m][t0], Nw[m][t0 + 1].
+template <int NT, int THREADS>
+__device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x, const float2* tw,
+                                                  int t0, bool hasb) {
+  fft_smem<NT, THREADS, false>(x, tw);
+  for (int m = threadIdx.x; m < s.nw; m += THREADS) {
+    const float2 zm = x[m];
+    const float2 zc = cconj(x[(NT - m) & (NT - 1)]);
+    const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
+    const float dx = zm.x - zc.x, dy = zm.y - zc.y;
+    const float2 B = hasb ? make_float2(0.5f * dy, -0.5f * dx) : make_float2(0.f, 0.f);
+    *reinterpret_cast<float4*>(s.Nw + (int64_t)m * s.nw_stride + t0) = make_float4(A.x, A.y, B.x, B.y);
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(threads_for(NT))
+epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
+  constexpr int THREADS = threads_for(NT);
+  constexpr int PJ = NT / THREADS;  // samples per thread
+  extern __shared__ float4 smem_raw[];
+  float2* x = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = x + NT;
+  __shared__ double red[2 * (THREADS / 32)];
+  __shared__ int s_last;
+
+  for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
+  __syncthreads();
+
+  const int npairs = (s.ncols + 1) / 2;
+  const float inv = s.inv_nt;
+  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+    const int t0 = 2 * p;
+    const bool hasb = t0 + 1 < s.ncols;
+    // 1. Hermitian pack of the two band spectra (bins outside the band are zero)
+    for (int m = threadIdx.x; m <= NT / 2; m += THREADS) {
+      float2 X = make_float2(0.f, 0.f), Y = make_float2(0.f, 0.f);
+      if (m < s.nw) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(s.S + (int64_t)m * s.s_stride + t0));
+        X = make_float2(v.x, v.y);
+        if (hasb) Y = make_float2(v.z, v.w);
+      }
+      if (m == 0 || m == NT / 2) {
+        X.y = 0.f;
+        Y.y = 0.f;
+      }
+      x[m] = make_float2(X.x - Y.y, X.y + Y.x);
+      if (m > 0 && m < NT / 2) x[NT - m] = make_float2(X.x + Y.y, Y.x - X.y);
+    }
+    __syncthreads();
+    // 2. inverse transform: x[j] = nt * (s_a(j) + i s_b(j))
+    fft_smem<NT, THREADS, true>(x, tw);
+    // 3. gather s(j) and s(-j)
+    float2 zj[PJ], zr[PJ];
+#pragma unroll
+    for (int q = 0; q < PJ; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      zj[q] = x[j];
+      zr[q] = x[(NT - j) & (NT - 1)];
+    }
+    __syncthreads();
+    // 4. reverse, negate, mute, accumulate; N_i back into x for the forward transform
+    const int La = s.L[t0];
+    const int Lb = hasb ? s.L[t0 + 1] : 0;
+    const int64_t ba = field_offset(s, t0);
+    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+    double ea = 0.0, eb = 0.0;
+#pragma unroll
+    for (int q = 0; q < PJ; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      const int d = j < NT - j ? j : NT - j;  // |signed index|
+      const float sa = zj[q].x * inv, sb = zj[q].y * inv;
+      const float na = d < La ? -(zr[q].x * inv) : 0.f;
+      const float nb = d < Lb ? -(zr[q].y * inv) : 0.f;
+      x[j] = make_float2(na, nb);
+      s.pmin[ba + j] += sa;
+      s.fN[ba + j] = na;
+      if (d < La) {
+        s.f2p[ba + j] += na;
+        if (odd) s.f1p[ba + j] += na;
+        else s.f1m[ba + j] += sa;  // f1min -= N_i(-t) = -theta s(t)
+        ea += (double)na * (double)na;
+      }
+      if (hasb) {
+        s.pmin[bb + j] += sb;
+        s.fN[bb + j] = nb;
+        if (d < Lb) {
+          s.f2p[bb + j] += nb;
+          if (odd) s.f1p[bb + j] += nb;
+          else s.f1m[bb + j] += sb;
+          eb += (double)nb * (double)nb;
+        }
+      }
+    }
+    __syncthreads();
+    // 5. forward transform of N_i, band spectra to Nw
+    forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
+    // 6. per-trace energies
+    block_sum2<THREADS>(ea, eb, red);
+    if (threadIdx.x == 0) {
+      s.Epart[t0] = ea;
+      if (hasb) s.Epart[t0 + 1] = eb;
+    }
+    __syncthreads();
+  }
+
+  // The last CTA to finish sums the per-trace energies per focal point in a
+  // fixed order (k ascending), so the result does not depend on scheduling.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(s.counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    for (int f = threadIdx.x; f < s.F; f += THREADS) {
+      double acc = 0.0;
+      for (int k = 0; k < s.ns; ++k) acc += __ldcg(s.Epart + (int64_t)k * s.F + f);
+      energy_slot[f] = acc;
+    }
+    if (threadIdx.x == 0) *s.counter = 0u;
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(threads_for(NT))
+init_kernel(SurveyDev s, const float* __restrict__ Gd) {
+  constexpr int THREADS = threads_for(NT);
+  constexpr int PJ = NT / THREADS;
+  extern __shared__ float4 smem_raw[];
+  float2* x = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = x + NT;
+  for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
+  __syncthreads();
+  const int npairs = (s.ncols + 1) / 2;
+  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+    const int t0 = 2 * p;
+    const bool hasb = t0 + 1 < s.ncols;
+    const int64_t ba = field_offset(s, t0);
+    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+#pragma unroll
+    for (int q = 0; q < PJ; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      const int jr = (NT - j) & (NT - 1);
+      const float na = Gd[ba + jr];  // G_d has the field layout [F][nrec][nt]
+      const float nb = hasb ? Gd[bb + jr] : 0.f;
+      x[j] = make_float2(na, nb);
+      s.fN[ba + j] = na;
+      s.f1p[ba + j] = na;
+      s.f2p[ba + j] = na;
+      s.f1m[ba + j] = 0.f;
+      s.pmin[ba + j] = 0.f;
+      if (hasb) {
+        s.fN[bb + j] = nb;
+        s.f1p[bb + j] = nb;
+        s.f2p[bb + j] = nb;
+        s.f1m[bb + j] = 0.f;
+        s.pmin[bb + j] = 0.f;
+      }
+    }
+    __syncthreads();
+    forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
+    __syncthreads();
+  }
+}
+
+// theta window half-length per trace: the number of n >= 0 with
+// n * dt < t_d - eps, evaluated in FP64 exactly as written (IEEE products and
+// differences, so every device and the host take the same decisions), capped
+// at nt/2 + 1 (everything kept).  Non-finite t_d gives an empty window.
+__global__ void window_kernel(SurveyDev s, const double* __restrict__ td, double eps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.ncols) return;
+  const int f = t % s.F, k = t / s.F;
+  const double T = td[(int64_t)f * s.ns + k] - eps;
+  int L = 0;
+  if (T > 0.0 && isfinite(T)) {
+    const double q = ceil(T / s.dt);
+    long long Lq = q > (double)s.nt ? (long long)s.nt : (long long)q;
+    if (Lq < 0) Lq = 0;
+    while (Lq > 0 && (double)(Lq - 1) * s.dt >= T) --Lq;
+    while (Lq <= s.nt / 2 && (double)Lq * s.dt < T) ++Lq;
+    L = (int)(Lq > s.nt / 2 + 1 ? s.nt / 2 + 1 : Lq);
+  }
+  s.L[t] = L;
+}
+
+__global__ void green_kernel(SurveyDev s, float* __restrict__ out) {
+  const int64_t total = (int64_t)s.F * s.ns * s.nt;
+  const int mask = s.nt - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i & mask);
+    const int64_t base = i - j;
+    out[i] = s.f2p[base + ((s.nt - j) & mask)] + s.pmin[i];
+  }
+}
+
+template <int NT>
+cudaError_t set_attrs() {
+  const int bytes = 2 * NT * (int)sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int NT>
+cudaError_t launch_epi_nt(const SurveyDev& s, int odd, double* slot, cudaStream_t st, int num_sms) {
+  const int npairs = (s.ncols + 1) / 2;
+  const int per_sm = NT >= 4096 ? 2 : 4;
+  int grid = num_sms * per_sm;
+  if (grid > npairs) grid = npairs;
+  const size_t bytes = 2 * NT * sizeof(float2);
+  epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, odd, slot);
+  return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_init_nt(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms) {
+  const int npairs = (s.ncols + 1) / 2;
+  int grid = num_sms * 4;
+  if (grid > npairs) grid = npairs;
+  const size_t bytes = 2 * NT * sizeof(float2);
+  init_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, Gd);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define MK_NT_SWITCH(nt, CALL)          \
+  switch (nt) {                         \
+    case 32: return CALL(32);           \
+    case 64: return CALL(64);           \
+    case 128: return CALL(128);         \
+    case 256: return CALL(256);         \
+    case 512: return CALL(512);         \
+    case 1024: return CALL(1024);       \
+    case 2048: return CALL(2048);       \
+    case 4096: return CALL(4096);       \
+    case 8192: return CALL(8192);       \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t prepare_kernels() {
+  cudaError_t e;
+#define MK_ATTR(N) \
+  if ((e = set_attrs<N>()) != cudaSuccess) return e;
+  MK_ATTR(32) MK_ATTR(64) MK_ATTR(128) MK_ATTR(256) MK_ATTR(512) MK_ATTR(1024) MK_ATTR(2048)
+  MK_ATTR(4096) MK_ATTR(8192)
+#undef MK_ATTR
+  return cudaSuccess;
+}
+
+cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
+                            int num_sms) {
+#define MK_CALL(N) launch_epi_nt<N>(s, odd, energy_slot, st, num_sms)
+  MK_NT_SWITCH(s.nt, MK_CALL)
+#undef MK_CALL
+}
+
+cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms) {
+#define MK_CALL(N) launch_init_nt<N>(s, Gd, st, num_sms)
+  MK_NT_SWITCH(s.nt, MK_CALL)
+#undef MK_CALL
+}
+
+cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st) {
+  window_kernel<<<(s.ncols + 255) / 256, 256, 0, st>>>(s, td, eps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms) {
+  green_kernel<<<num_sms * 8, 256, 0, st>>>(s, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mk

@@ -1,0 +1,53 @@
+// Internal declarations shared by the host API and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mk {
+
+// Device-side view of one survey: sizes, strides and workspace carvings.
+// Trace ("column") index t = k * F + f; field offset of trace (k, f) is
+// (f * ns + k) * nt.  S and Nw are frequency-major: element (m, t) lives at
+// m * s_stride + t (S) and m * nw_stride + t (Nw).  For F = 1, Nw rows are
+// r_pad long and the entries t >= ns stay zero.
+struct SurveyDev {
+  int ns;          // positions (nsrc == nrec)
+  int nt;          // samples
+  int F;           // focal points
+  int nw;          // kept frequency bins
+  int r_pad;       // padded row length of R (multiple of 32)
+  int ncols;       // ns * F
+  int64_t s_stride;   // complex elements per S row (>= ncols + 1, multiple of 4)
+  int64_t nw_stride;  // complex elements per Nw row (r_pad * F)
+  double dt;       // sample interval (s)
+  float c;         // synthesis scale dx * dt
+  float inv_nt;    // 1 / nt
+  int rprec;       // mk_rprec
+
+  const float2* R;  // [nw][ns][r_pad] complex FP32 (MK_R_C64)
+  float2* Nw;       // [nw][nw_stride]
+  float2* S;        // [nw][s_stride]
+  float* fN;        // [F][ns][nt] last N_i
+  float* f1p;
+  float* f1m;
+  float* f2p;
+  float* pmin;
+  float* scratch;   // [F][ns][nt] staging (G_d upload, G for host output)
+  int* L;           // [ncols] window half-lengths
+  double* td;       // [F][ns] staging of t_d uploaded from the host
+  double* Epart;    // [ncols + 1] per-trace energies
+  unsigned* counter;  // last-block counter of the epilogue
+  const float2* tw;   // [nt] e^{-2 pi i q / nt}
+};
+
+// Kernel launchers (return the launch status; the caller checks it).
+cudaError_t launch_contract(const SurveyDev& s, cudaStream_t st, int num_sms, int* nlaunch);
+cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
+                            int num_sms);
+cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);
+cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st);
+cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms);
+cudaError_t prepare_kernels();  // one-time function attributes (large dynamic smem)
+
+}  // namespace mk

@@ -1,0 +1,159 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import marchenko as M
+from tests.conftest import rel_l2, small_survey
+from tests.helpers import FIELD_NAMES, desc_for, survey_inputs
+
+pytestmark = pytest.mark.gpu
+
+# relative L2 gates (float32 path vs FP64 oracle)
+TOL_ITER = 1e-5     # accumulated fields, every iteration
+TOL_N = 1e-4        # the current N_i (a small, shrinking term) and after 16 iterations
+TOL_E = 1e-4        # energies
+
+
+def _plan(survey, R, Gd, td, nfocal=None):
+    from paper_2106_04649_gb300.api import Plan
+    p = Plan([desc_for(survey, nfocal=nfocal)])
+    p.load_R(0, R)
+    p.set_Gd_window(0, Gd, td, survey.eps)
+    return p
+
+
+def _oracle_fields(st):
+    return [st.N, st.f1plus, st.f1min, st.f2p, st.pmin, M.total_green(st.f2p, st.pmin)]
+
+
+def _compare(fields, st, tol_acc, tol_n, label=""):
+    ref = _oracle_fields(st)
+    errs = {name: rel_l2(fields[i], ref[i]) for i, name in enumerate(FIELD_NAMES)}
+    for name, e in errs.items():
+        tol = tol_n if name == "N" else tol_acc
+        assert e <= tol, f"{label} {name}: rel L2 {e:.3e} > {tol:.0e} ({errs})"
+    return errs
+
+
+def test_tiny_trajectory_16_iterations(tiny_inputs):
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    _, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 16, history=True)
+    p = _plan(s, R, Gd, td)
+    f0 = p.fetch_fields(0)
+    st0 = M.initialise(Gd.astype(np.float64))
+    _compare(f0, st0, 1e-7, 1e-7, "init")
+    for i in range(16):
+        e = p.iterate(1)
+        f = p.fetch_fields(0)
+        _compare(f, hist[i], TOL_ITER, TOL_N, f"iter {i}")
+        assert abs(e[0, 0] - hist[i].energy[i][0]) <= TOL_E * hist[i].energy[i][0]
+    p.close()
+
+
+def test_tiny_energies_match_oracle(tiny_inputs):
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    st = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 16)
+    p = _plan(s, R, Gd, td)
+    e = p.iterate(16)
+    assert e.shape == (16, 1)
+    assert np.max(np.abs(e[:, 0] - np.array(st.energy)[:, 0]) / np.array(st.energy)[:, 0]) <= TOL_E
+    _compare(p.fetch_fields(0), st, TOL_N, TOL_N, "after 16")
+    p.close()
+
+
+@pytest.mark.parametrize("n,nt,nfocal,fmax", [(25, 128, 2, None), (25, 128, 3, 40.0), (7, 32, 1, None),
+                                              (1, 64, 1, None), (3, 64, 2, 30.0), (33, 256, 1, 50.0)])
+def test_small_ragged_surveys(n, nt, nfocal, fmax):
+    s = small_survey(n=n, nt=nt, nfocal=min(nfocal, 3), fmax_hz=fmax)
+    R, td, Gd = survey_inputs(s)
+    st, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 6, history=True)
+    p = _plan(s, R, Gd, td)
+    for i in range(6):
+        p.iterate(1)
+        _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"n={n} nt={nt} F={nfocal} iter {i}")
+    p.close()
+
+
+def test_deterministic_repeat(tiny_inputs):
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    out = []
+    for _ in range(2):
+        p = _plan(s, R, Gd, td)
+        e = p.iterate(5)
+        out.append((e, p.fetch_fields(0)))
+        p.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_restart_resets_series(tiny_inputs):
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    p = _plan(s, R, Gd, td)
+    e1 = p.iterate(3)
+    p.set_Gd_window(0, Gd, td, s.eps)
+    e2 = p.iterate(3)
+    assert np.array_equal(e1, e2)
+    p.close()
+
+
+def test_paper_small_F1_full_size():
+    s = S.paper_small_survey(1)
+    R, td, Gd = survey_inputs(s)
+    st = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 16)
+    p = _plan(s, R, Gd, td)
+    e = p.iterate(16)
+    _compare(p.fetch_fields(0), st, TOL_N, TOL_N, "paper-small F=1 after 16")
+    ref = np.array(st.energy)[:, 0]
+    assert np.max(np.abs(e[:, 0] - ref) / ref) <= TOL_E
+    p.close()
+
+
+def test_device_inputs_and_outputs(tiny_inputs):
+    import torch
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    from paper_2106_04649_gb300.api import Plan
+    p = Plan([desc_for(s)])
+    p.load_R(0, torch.from_numpy(R).cuda())
+    p.set_Gd_window(0, torch.from_numpy(Gd).cuda(), torch.from_numpy(td).cuda(), s.eps)
+    p.iterate(4)
+    dev = torch.empty((6, 1, s.n, s.nt), dtype=torch.float32, device="cuda")
+    p.fetch_fields(0, out=dev)
+    host = p.fetch_fields(0)
+    assert np.array_equal(dev.cpu().numpy(), host)
+    p.close()
+
+
+def test_call_order_errors(tiny_inputs):
+    from paper_2106_04649_gb300.api import Plan
+    from paper_2106_04649_gb300.binding import MarchenkoError
+    from paper_2106_04649_gb300 import _native as N
+    s, R64, td, Gd64 = tiny_inputs
+    p = Plan([desc_for(s)])
+    with pytest.raises(MarchenkoError) as ei:
+        p.iterate(1)
+    assert ei.value.status == N.MK_ERR_STATE
+    p.load_R(0, R64[:10].astype(np.complex64))
+    with pytest.raises(MarchenkoError) as ei:
+        p.set_Gd_window(0, Gd64, td, s.eps)
+    assert ei.value.status == N.MK_ERR_STATE
+    with pytest.raises(MarchenkoError) as ei:
+        p.load_R(0, R64[:10].astype(np.complex64), w_begin=250)
+    assert ei.value.status == N.MK_ERR_ARG
+    from paper_2106_04649_gb300 import binding as B
+    out = np.empty(8, dtype=np.float32)
+    with pytest.raises(MarchenkoError) as ei:
+        B.mk_fetch_fields(p.handle, 5, N.MK_F_N, out.ctypes.data, out.nbytes, False)
+    assert ei.value.status == N.MK_ERR_ARG
+    p.close()
