@@ -204,6 +204,46 @@ mk_status mk_fetch_fields(mk_plan_t plan, int32_t survey, uint32_t mask, float* 
  */
 mk_status mk_get_stats(mk_plan_t plan, mk_stats_t* out, int32_t reset);
 
+/*
+ * mk_run_noalloc - the same computation as mk_set_Gd_window followed by
+ * mk_iterate(niter) for one survey, for callers that cannot allocate device
+ * memory.  The paper has no counterpart; it exists because some callers
+ * cannot call cudaMalloc at the point of use (a host framework that owns all
+ * GPU memory through its own pool and passes only fixed input and output
+ * buffers, or a process with a memory budget fixed in advance) and so cannot
+ * provide the plan workspace of mk_plan.
+ *
+ * It allocates nothing: it calls no cudaMalloc, cudaFree or allocating
+ * library routine.  Its intermediate data (mute windows, band spectra, per-
+ * trace energies, FFT twiddles) lives in one file-scope device array of
+ * MK_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library
+ * holds until the process exits.  Surveys that need more scratch than that
+ * (about 2 * n_w * r_pad * nfocal * 8 bytes) are rejected with MK_ERR_ARG
+ * before any GPU work.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and sets kernel attributes; make that first call
+ * before any stream capture.  Every call uses the same array and the array
+ * keeps the last call's contents (each call clears what it needs zeroed), so
+ * calls whose GPU work overlaps -- on different streams, or from different
+ * threads -- race with each other: order them on one stream.
+ *
+ *   d:      one survey (rprec must be MK_R_C64).
+ *   R:      device, complex64 [n_w][nsrc][r_pad], r_pad = nrec rounded up to
+ *           a multiple of 32, padding entries zero (the plan's R layout).
+ *   Gd, td: device, as for mk_set_Gd_window.
+ *   niter:  iterations (>= 0).
+ *   fields: device float [5][nfocal][nsrc][nt]: N, f1plus, f1min, f2p, pmin
+ *           after niter iterations (written, not read).
+ *   energy: device double [niter][nfocal], or NULL.
+ *   cuda_stream: stream for all the work; the call returns without waiting.
+ * Errors (message via mk_last_error(NULL)): MK_ERR_ARG, MK_ERR_UNSUPPORTED,
+ *         MK_ERR_CUDA.
+ */
+#define MK_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float* Gd, const double* td, double eps_s,
+                         int32_t niter, float* fields, double* energy, void* cuda_stream);
+
 /* mk_destroy - release the plan's host state (not the caller's workspace).
  * Synchronises the plan's stream.  NULL is accepted. */
 mk_status mk_destroy(mk_plan_t plan);

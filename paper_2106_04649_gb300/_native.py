@@ -59,7 +59,10 @@ _SIGS = {
     "mk_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(MkStats), ctypes.c_int32]),
     "mk_destroy": (ctypes.c_int, [_P]),
     "mk_last_error": (ctypes.c_char_p, [_P]),
+    "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,
+                                      _P]),
 }
+MK_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
 

@@ -76,3 +76,11 @@ def mk_destroy(plan: int) -> None:
 def mk_last_error(plan: int | None) -> str:
     msg = N.load().mk_last_error(plan)
     return msg.decode() if msg else ""
+
+
+def mk_run_noalloc(desc, R: int, Gd: int, td: int, eps_s: float, niter: int, fields: int, energy: int | None,
+                   cuda_stream: int) -> None:
+    """No-allocation run (device pointers only); errors via mk_last_error(None)."""
+    arr, _ = _descs([desc])
+    _check(N.load().mk_run_noalloc(arr, R, Gd, td, eps_s, niter, fields, energy, ctypes.c_void_p(cuda_stream)),
+           None)

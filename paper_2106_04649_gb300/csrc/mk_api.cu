@@ -172,6 +172,10 @@ TimedPair* next_pair(mk_plan_t p, int kind) {
 
 }  // namespace
 
+namespace mk {
+void set_noplan_error(const char* msg) { snprintf(g_noplan_err, sizeof g_noplan_err, "%s", msg); }
+}  // namespace mk
+
 extern "C" {
 
 mk_status mk_workspace_size(const mk_desc* d, int32_t ndesc, size_t* bytes) {

@@ -49,5 +49,6 @@ cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, in
 cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st);
 cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms);
 cudaError_t prepare_kernels();  // one-time function attributes (large dynamic smem)
+void set_noplan_error(const char* msg);  // message returned by mk_last_error(NULL)
 
 }  // namespace mk
