@@ -124,21 +124,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    with open(os.path.join(ROOT, "paper_2106_04649_gb300", "csrc", "mk_contract.cu"), "rb") as f:
+def kernel_source_hash(src: str) -> str:
+    with open(os.path.join(ROOT, "paper_2106_04649_gb300", "csrc", src), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def profiled_traffic(workload_key: str):
     """DRAM bytes per contraction launch from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+    when the kernel's source file changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     e = d.get(workload_key)
-    if not e or e.get("source_sha256_16") != kernel_source_hash():
+    if not e or e.get("source_sha256_16") != kernel_source_hash(e.get("source", "")):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -196,6 +196,22 @@ mk_status mk_fetch_fields(mk_plan_t plan, int32_t survey, uint32_t mask, float* 
                           size_t out_bytes, int32_t dst_on_device);
 
 /*
+ * mk_set_fields - resume a series from saved fields (checkpoint / restart;
+ * the paper's GPU code keeps iRN on disk between iterations, Algorithm 1).
+ * Overwrites the selected fields of one survey with caller data, sets the
+ * iteration index (its parity decides f1min vs f1plus, Algorithm 1) and
+ * recomputes the band spectrum of N from the (new) N field, so that the next
+ * mk_iterate continues from exactly these fields.  Windows stay those of the
+ * last mk_set_Gd_window.
+ *   mask: MK_F_N | MK_F_F1P | MK_F_F1M | MK_F_F2P | MK_F_PMIN subset (not MK_F_G);
+ *   in:   float [popcount(mask)][nfocal][nsrc][nt] in bit order, host or device.
+ *   iteration: the number of iterations these fields represent (>= 0).
+ * Errors: MK_ERR_ARG, MK_ERR_STATE (G_d not set), MK_ERR_CUDA.
+ */
+mk_status mk_set_fields(mk_plan_t plan, int32_t survey, uint32_t mask, const float* in, size_t in_bytes,
+                        int32_t iteration, int32_t src_on_device);
+
+/*
  * mk_get_stats - launch counters and (with MK_FLAG_TIMING on every survey's
  * description) summed CUDA-event times of the contraction and epilogue
  * kernels, measured on the plan's stream.  Synchronises the stream.

@@ -57,6 +57,8 @@ _SIGS = {
     "mk_iterate": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "mk_fetch_fields": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, _P, ctypes.c_size_t, ctypes.c_int32]),
     "mk_get_stats": (ctypes.c_int, [_P, ctypes.POINTER(MkStats), ctypes.c_int32]),
+    "mk_set_fields": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint32, _P, ctypes.c_size_t, ctypes.c_int32,
+                                     ctypes.c_int32]),
     "mk_destroy": (ctypes.c_int, [_P]),
     "mk_last_error": (ctypes.c_char_p, [_P]),
     "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,

@@ -108,6 +108,15 @@ class Plan:
             B.mk_fetch_fields(self.handle, survey, mask, out.ctypes.data, out.nbytes, False)
         return out
 
+    def set_fields(self, survey: int, fields, iteration: int, mask: int = 0x1F) -> None:
+        """Resume from saved fields [popcount(mask)][F][n][nt] (N, f1plus, f1min, f2p, pmin order)."""
+        if isinstance(fields, torch.Tensor):
+            assert fields.is_cuda and fields.dtype == torch.float32 and fields.is_contiguous()
+            B.mk_set_fields(self.handle, survey, mask, fields.data_ptr(), fields.numel() * 4, iteration, True)
+        else:
+            a, ptr = _ptr_host(fields, np.float32)
+            B.mk_set_fields(self.handle, survey, mask, ptr, a.nbytes, iteration, False)
+
     def stats(self, reset: bool = False) -> dict:
         return B.mk_get_stats(self.handle, reset)
 

@@ -63,6 +63,11 @@ def mk_fetch_fields(plan: int, survey: int, mask: int, out: int, out_bytes: int,
     _check(N.load().mk_fetch_fields(plan, survey, mask, out, out_bytes, int(dst_on_device)), plan)
 
 
+def mk_set_fields(plan: int, survey: int, mask: int, data: int, nbytes: int, iteration: int,
+                  src_on_device: bool) -> None:
+    _check(N.load().mk_set_fields(plan, survey, mask, data, nbytes, iteration, int(src_on_device)), plan)
+
+
 def mk_get_stats(plan: int, reset: bool = False) -> dict:
     st = N.MkStats()
     _check(N.load().mk_get_stats(plan, ctypes.byref(st), int(reset)), plan)

@@ -24,6 +24,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Survey {
   mk_desc d;
   mk::SurveyDev dev;
+  mk::UmmaMaps* umma = nullptr;  // tensor maps (16-bit R precisions)
   double* energy = nullptr;  // [kMaxIterSlots][F] device
   std::vector<unsigned char> loaded;
   int nloaded = 0;
@@ -89,9 +90,8 @@ mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nt=%d must be a power of two in [32, 8192]", i, d.nt);
   if (!(d.dt > 0.0) || !(d.dx > 0.0) || !isfinite(d.dt) || !isfinite(d.dx))
     return fail(p, MK_ERR_ARG, "survey %d: dt and dx must be finite and > 0", i);
-  if (d.rprec != MK_R_C64)
-    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: R storage precision %d not available in this build", i,
-                d.rprec);
+  if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT_BF16)
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: unknown R storage precision %d", i, d.rprec);
   if ((int64_t)d.nsrc * d.nfocal > (int64_t)1 << 30)
     return fail(p, MK_ERR_ARG, "survey %d: nsrc * nfocal too large", i);
   return MK_OK;
@@ -120,8 +120,22 @@ size_t layout(Survey& sv, char* base) {
     return ptr;
   };
   const size_t field = (size_t)v.F * v.ns * v.nt * sizeof(float);
-  v.R = reinterpret_cast<const float2*>(take((size_t)v.nw * v.ns * v.r_pad * sizeof(float2)));
-  v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
+  if (d.rprec == MK_R_C64) {
+    v.R = reinterpret_cast<const float2*>(take((size_t)v.nw * v.ns * v.r_pad * sizeof(float2)));
+    v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
+    v.Rq0 = v.Rq1 = nullptr;
+    v.Bq0 = v.Bq1 = nullptr;
+  } else {
+    // 16-bit interleaved complex rows of 2 r_pad values; field embedding [nw][2F][2 r_pad]
+    const size_t rq = (size_t)v.nw * v.ns * 2 * v.r_pad * 2;
+    const size_t bq = (size_t)v.nw * 2 * v.F * 2 * v.r_pad * 2;
+    v.R = nullptr;
+    v.Nw = nullptr;
+    v.Rq0 = take(rq);
+    v.Rq1 = d.rprec == MK_R_SPLIT_BF16 ? take(rq) : nullptr;
+    v.Bq0 = take(bq);
+    v.Bq1 = take(bq);
+  }
   v.S = reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)));
   v.fN = reinterpret_cast<float*>(take(field));
   v.f1p = reinterpret_cast<float*>(take(field));
@@ -133,6 +147,7 @@ size_t layout(Survey& sv, char* base) {
   v.td = reinterpret_cast<double*>(take((size_t)v.ncols * sizeof(double)));
   v.Epart = reinterpret_cast<double*>(take((size_t)(v.ncols + 1) * sizeof(double)));
   v.counter = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
+  v.err = reinterpret_cast<int*>(take(sizeof(int)));
   v.tw = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));
   sv.energy = reinterpret_cast<double*>(take((size_t)kMaxIterSlots * v.F * sizeof(double)));
   return off;
@@ -151,6 +166,21 @@ mk_status ensure_device(mk_plan_t p) {
   MK_CUDA(p, cudaGetDevice(&dev));
   if (dev != p->device)
     return fail(p, MK_ERR_STATE, "current device %d is not the plan's device %d", dev, p->device);
+  return MK_OK;
+}
+
+// Reads and clears the device error words (after a stream synchronisation).
+mk_status check_device_errors(mk_plan_t p) {
+  for (size_t i = 0; i < p->s.size(); ++i) {
+    int h = 0;
+    MK_CUDA(p, cudaMemcpyAsync(&h, p->s[i].dev.err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    MK_CUDA(p, cudaStreamSynchronize(p->stream));
+    if (h != 0) {
+      MK_CUDA(p, cudaMemsetAsync(p->s[i].dev.err, 0, sizeof(int), p->stream));
+      return fail(p, MK_ERR_TIMEOUT, "survey %d: a bounded device wait ran out (code %d); results are invalid",
+                  (int)i, h);
+    }
+  }
   return MK_OK;
 }
 
@@ -245,6 +275,14 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
     return fail(nullptr, MK_ERR_CUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
   }
   for (auto& sv : p->s) {
+    if (sv.d.rprec != MK_R_C64) {
+      sv.umma = mk::umma_create(sv.dev);
+      if (!sv.umma) {
+        for (auto& o : p->s) mk::umma_destroy(o.umma);
+        delete p;
+        return fail(nullptr, MK_ERR_CUDA, "tensor map encoding for the tensor-core contraction failed");
+      }
+    }
     const int nt = sv.dev.nt;
     std::vector<float2> tw(nt);
     for (int q = 0; q < nt; ++q) {
@@ -255,6 +293,7 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
                         p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
+      for (auto& o : p->s) mk::umma_destroy(o.umma);
       delete p;
       return fail(nullptr, MK_ERR_CUDA, "twiddle upload failed: %s", cudaGetErrorString(e));
     }
@@ -275,10 +314,52 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
   if (w_begin < 0 || w_count < 0 || w_begin + w_count > v.nw)
     return fail(p, MK_ERR_ARG, "bins [%d, %d) outside the band [0, %d)", w_begin, w_begin + w_count, v.nw);
   if (w_count == 0) return MK_OK;
-  float2* dst = const_cast<float2*>(v.R) + (size_t)w_begin * v.ns * v.r_pad;
-  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  MK_CUDA(p, cudaMemcpy2DAsync(dst, (size_t)v.r_pad * sizeof(float2), Rw, (size_t)v.ns * sizeof(float2),
-                               (size_t)v.ns * sizeof(float2), (size_t)w_count * v.ns, kind, p->stream));
+  const int64_t rows = (int64_t)w_count * v.ns;
+  const int64_t row0 = (int64_t)w_begin * v.ns;
+  const float2* src = static_cast<const float2*>(Rw);
+  bool direct = src_on_device != 0;
+  if (!direct) {
+    // pinned (page-locked) host memory is read by the kernel in place
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, Rw);
+    if (e == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer) {
+      src = static_cast<const float2*>(attr.devicePointer);
+      direct = true;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (v.rprec == MK_R_C64) {
+    float2* dst = const_cast<float2*>(v.R) + row0 * v.r_pad;
+    if (direct) {
+      MK_CUDA(p, mk::launch_load_rows(src, dst, rows, v.ns, v.r_pad, p->stream, p->num_sms));
+      p->stats.launches++;
+      p->stats.other_launches++;
+    } else {
+      // pageable host memory: the driver stages the copy
+      MK_CUDA(p, cudaMemcpy2DAsync(dst, (size_t)v.r_pad * sizeof(float2), Rw, (size_t)v.ns * sizeof(float2),
+                                   (size_t)v.ns * sizeof(float2), (size_t)rows, cudaMemcpyHostToDevice,
+                                   p->stream));
+    }
+  } else if (direct) {
+    MK_CUDA(p, mk::launch_load_rows_q(src, v, row0, rows, p->stream, p->num_sms));
+    p->stats.launches++;
+    p->stats.other_launches++;
+  } else {
+    // pageable host memory into 16-bit storage: chunks through the scratch field
+    const size_t scratch_bytes = (size_t)v.F * v.ns * v.nt * sizeof(float);
+    int64_t chunk = (int64_t)(scratch_bytes / ((size_t)v.ns * sizeof(float2)));
+    if (chunk < 1) return fail(p, MK_ERR_UNSUPPORTED, "pageable R rows larger than the staging area");
+    for (int64_t r = 0; r < rows; r += chunk) {
+      const int64_t n = rows - r < chunk ? rows - r : chunk;
+      MK_CUDA(p, cudaMemcpyAsync(v.scratch, static_cast<const float2*>(Rw) + r * v.ns,
+                                 (size_t)n * v.ns * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+      MK_CUDA(p, mk::launch_load_rows_q(reinterpret_cast<const float2*>(v.scratch), v, row0 + r, n, p->stream,
+                                        p->num_sms));
+      p->stats.launches++;
+      p->stats.other_launches++;
+    }
+  }
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   for (int m = w_begin; m < w_begin + w_count; ++m) {
     if (!sv->loaded[m]) {
@@ -340,7 +421,7 @@ mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
         TimedPair* tp = next_pair(p, 0);
         if (tp) MK_CUDA(p, cudaEventRecord(tp->a, p->stream));
         int nl = 0;
-        MK_CUDA(p, mk::launch_contract(sv.dev, p->stream, p->num_sms, &nl));
+        MK_CUDA(p, mk::launch_contract(sv.dev, sv.umma, p->stream, p->num_sms, &nl));
         if (tp) MK_CUDA(p, cudaEventRecord(tp->b, p->stream));
         p->stats.launches += nl;
         p->stats.contract_launches += nl;
@@ -364,6 +445,7 @@ mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
         foff += sv.dev.F;
       }
       MK_CUDA(p, cudaStreamSynchronize(p->stream));
+      if ((st = check_device_errors(p)) != MK_OK) return st;
     }
     done += chunk;
   }
@@ -401,7 +483,42 @@ mk_status mk_fetch_fields(mk_plan_t p, int32_t survey, uint32_t mask, float* out
     }
     o += field;
   }
-  if (!dst_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  if (!dst_on_device) {
+    MK_CUDA(p, cudaStreamSynchronize(p->stream));
+    if ((st = check_device_errors(p)) != MK_OK) return st;
+  }
+  return MK_OK;
+}
+
+mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float* in, size_t in_bytes,
+                        int32_t iteration, int32_t src_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!in) return fail(p, MK_ERR_ARG, "null input pointer");
+  if (mask == 0 || (mask & ~(MK_F_N | MK_F_F1P | MK_F_F1M | MK_F_F2P | MK_F_PMIN)))
+    return fail(p, MK_ERR_ARG, "field mask 0x%x invalid (MK_F_G cannot be set)", mask);
+  if (iteration < 0) return fail(p, MK_ERR_ARG, "iteration < 0");
+  if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
+  const mk::SurveyDev& v = sv->dev;
+  const size_t field = (size_t)v.F * v.ns * v.nt;
+  const size_t need = (size_t)__builtin_popcount(mask) * field * sizeof(float);
+  if (in_bytes < need) return fail(p, MK_ERR_ARG, "input of %zu bytes, %zu needed", in_bytes, need);
+  const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  float* dst[5] = {v.fN, v.f1p, v.f1m, v.f2p, v.pmin};
+  const float* q = in;
+  for (int b = 0; b < 5; ++b) {
+    if (!(mask & (1u << b))) continue;
+    MK_CUDA(p, cudaMemcpyAsync(dst[b], q, field * sizeof(float), kind, p->stream));
+    q += field;
+  }
+  MK_CUDA(p, mk::launch_spectrum(v, p->stream, p->num_sms));
+  p->stats.launches++;
+  p->stats.other_launches++;
+  if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  sv->iter = iteration;
   return MK_OK;
 }
 
@@ -425,7 +542,7 @@ mk_status mk_get_stats(mk_plan_t p, mk_stats_t* out, int32_t reset) {
   }
   *out = p->stats;
   if (reset) p->stats = mk_stats_t{};
-  return MK_OK;
+  return check_device_errors(p);
 }
 
 mk_status mk_destroy(mk_plan_t p) {
@@ -435,6 +552,7 @@ mk_status mk_destroy(mk_plan_t p) {
     cudaEventDestroy(tp.a);
     cudaEventDestroy(tp.b);
   }
+  for (auto& sv : p->s) mk::umma_destroy(sv.umma);
   delete p;
   return MK_OK;
 }

@@ -17,6 +17,9 @@
 // table rounded to FP32.  One CTA processes one pair of traces at a time and
 // loops over pairs (grid sized to the SM count).
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "mk_internal.h"
 
 namespace mk {
@@ -156,8 +159,43 @@ __device__ __forceinline__ int64_t field_offset(const SurveyDev& s, int t) {
   return ((int64_t)f * s.ns + k) * s.nt;
 }
 
+// Two 16-bit values packed in 32 bits (low half first in memory).
+template <bool BF16>
+__device__ __forceinline__ uint32_t pack2(float a, float b) {
+  if (BF16) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  } else {
+    const __half2 v = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  }
+}
+template <bool BF16>
+__device__ __forceinline__ float round16(float a) {
+  return BF16 ? __bfloat162float(__float2bfloat16_rn(a)) : __half2float(__float2half_rn(a));
+}
+
+// Band value N = (nr, ni) of trace t at bin m into the K-major real
+// embedding of the tensor-core contraction, split into hi + lo 16-bit parts:
+// rows 2f: (Nr, -Ni), 2f+1: (Ni, Nr) at columns 2k, 2k+1.
+template <bool BF16>
+__device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int t, float nr, float ni) {
+  const int f = t % s.F, k = t / s.F;
+  const float hr = round16<BF16>(nr), hi = round16<BF16>(ni);
+  const float lr = nr - hr, li = ni - hi;
+  const int64_t kp = 2 * (int64_t)s.r_pad;
+  const int64_t e0 = ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k;
+  uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
+  uint32_t* b1 = reinterpret_cast<uint32_t*>(s.Bq1);
+  b0[e0 >> 1] = pack2<BF16>(hr, -hi);
+  b0[(e0 + kp) >> 1] = pack2<BF16>(hi, hr);
+  b1[e0 >> 1] = pack2<BF16>(lr, -li);
+  b1[(e0 + kp) >> 1] = pack2<BF16>(li, lr);
+}
+
 // Forward transform of the pair held in x (a + i b), unpacked into the band
-// spectra A_m, B_m for m < nw and written to Nw[m][t0], Nw[m][t0 + 1].
+// spectra A_m, B_m for m < nw and written to Nw[m][t0], Nw[m][t0 + 1]
+// (complex FP32 R) or into the 16-bit embedding (tensor-core precisions).
 template <int NT, int THREADS>
 __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x, const float2* tw,
                                                   int t0, bool hasb) {
@@ -168,18 +206,28 @@ __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x,
     const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
     const float dx = zm.x - zc.x, dy = zm.y - zc.y;
     const float2 B = hasb ? make_float2(0.5f * dy, -0.5f * dx) : make_float2(0.f, 0.f);
-    *reinterpret_cast<float4*>(s.Nw + (int64_t)m * s.nw_stride + t0) = make_float4(A.x, A.y, B.x, B.y);
+    if (s.rprec == 0) {
+      *reinterpret_cast<float4*>(s.Nw + (int64_t)m * s.nw_stride + t0) = make_float4(A.x, A.y, B.x, B.y);
+    } else if (s.rprec == 2) {
+      store_embedding<false>(s, m, t0, A.x, A.y);
+      if (hasb) store_embedding<false>(s, m, t0 + 1, B.x, B.y);
+    } else {
+      store_embedding<true>(s, m, t0, A.x, A.y);
+      if (hasb) store_embedding<true>(s, m, t0 + 1, B.x, B.y);
+    }
   }
 }
 
 template <int NT>
-__global__ void __launch_bounds__(threads_for(NT))
+__global__ void __launch_bounds__(threads_for(NT), NT <= 2048 ? 2 : 1)
 epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
   constexpr int THREADS = threads_for(NT);
   constexpr int PJ = NT / THREADS;  // samples per thread
+  constexpr int CH = PJ < 4 ? PJ : 4;  // samples per batch of field loads
   extern __shared__ float4 smem_raw[];
-  float2* x = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = x + NT;
+  float2* x = reinterpret_cast<float2*>(smem_raw);  // inverse transform
+  float2* y = x + NT;                               // N_i pair for the forward transform
+  float2* tw = y + NT;
   __shared__ double red[2 * (THREADS / 32)];
   __shared__ int s_last;
 
@@ -188,6 +236,10 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
 
   const int npairs = (s.ncols + 1) / 2;
   const float inv = s.inv_nt;
+  float* __restrict__ pmin = s.pmin;
+  float* __restrict__ fN = s.fN;
+  float* __restrict__ f2p = s.f2p;
+  float* __restrict__ f1 = odd ? s.f1p : s.f1m;
   for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int t0 = 2 * p;
     const bool hasb = t0 + 1 < s.ncols;
@@ -209,52 +261,59 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
     __syncthreads();
     // 2. inverse transform: x[j] = nt * (s_a(j) + i s_b(j))
     fft_smem<NT, THREADS, true>(x, tw);
-    // 3. gather s(j) and s(-j)
-    float2 zj[PJ], zr[PJ];
-#pragma unroll
-    for (int q = 0; q < PJ; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      zj[q] = x[j];
-      zr[q] = x[(NT - j) & (NT - 1)];
-    }
-    __syncthreads();
-    // 4. reverse, negate, mute, accumulate; N_i back into x for the forward transform
+    // 3. reverse, negate, mute, accumulate; N_i into y.  Field loads of a
+    //    batch of samples are issued before its stores (distinct arrays).
     const int La = s.L[t0];
     const int Lb = hasb ? s.L[t0 + 1] : 0;
     const int64_t ba = field_offset(s, t0);
     const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
     double ea = 0.0, eb = 0.0;
 #pragma unroll
-    for (int q = 0; q < PJ; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      const int d = j < NT - j ? j : NT - j;  // |signed index|
-      const float sa = zj[q].x * inv, sb = zj[q].y * inv;
-      const float na = d < La ? -(zr[q].x * inv) : 0.f;
-      const float nb = d < Lb ? -(zr[q].y * inv) : 0.f;
-      x[j] = make_float2(na, nb);
-      s.pmin[ba + j] += sa;
-      s.fN[ba + j] = na;
-      if (d < La) {
-        s.f2p[ba + j] += na;
-        if (odd) s.f1p[ba + j] += na;
-        else s.f1m[ba + j] += sa;  // f1min -= N_i(-t) = -theta s(t)
-        ea += (double)na * (double)na;
+    for (int q0 = 0; q0 < PJ; q0 += CH) {
+      float pa[CH], pb[CH], ga[CH], gb[CH], ha[CH], hb[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int j = threadIdx.x + (q0 + q) * THREADS;
+        const int d = j < NT - j ? j : NT - j;
+        pa[q] = pmin[ba + j];
+        ga[q] = d < La ? f2p[ba + j] : 0.f;
+        ha[q] = d < La ? f1[ba + j] : 0.f;
+        pb[q] = hasb ? pmin[bb + j] : 0.f;
+        gb[q] = (hasb && d < Lb) ? f2p[bb + j] : 0.f;
+        hb[q] = (hasb && d < Lb) ? f1[bb + j] : 0.f;
       }
-      if (hasb) {
-        s.pmin[bb + j] += sb;
-        s.fN[bb + j] = nb;
-        if (d < Lb) {
-          s.f2p[bb + j] += nb;
-          if (odd) s.f1p[bb + j] += nb;
-          else s.f1m[bb + j] += sb;
-          eb += (double)nb * (double)nb;
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int j = threadIdx.x + (q0 + q) * THREADS;
+        const int d = j < NT - j ? j : NT - j;  // |signed index|
+        const float2 zj = x[j];
+        const float2 zr = x[(NT - j) & (NT - 1)];
+        const float sa = zj.x * inv, sb = zj.y * inv;
+        const float na = d < La ? -(zr.x * inv) : 0.f;
+        const float nb = d < Lb ? -(zr.y * inv) : 0.f;
+        y[j] = make_float2(na, nb);
+        pmin[ba + j] = pa[q] + sa;
+        fN[ba + j] = na;
+        if (d < La) {
+          f2p[ba + j] = ga[q] + na;
+          f1[ba + j] = ha[q] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
+          ea += (double)na * (double)na;
+        }
+        if (hasb) {
+          pmin[bb + j] = pb[q] + sb;
+          fN[bb + j] = nb;
+          if (d < Lb) {
+            f2p[bb + j] = gb[q] + nb;
+            f1[bb + j] = hb[q] + (odd ? nb : sb);
+            eb += (double)nb * (double)nb;
+          }
         }
       }
     }
     __syncthreads();
-    // 5. forward transform of N_i, band spectra to Nw
-    forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
-    // 6. per-trace energies
+    // 4. forward transform of N_i, band spectra to Nw
+    forward_band_pair<NT, THREADS>(s, y, tw, t0, hasb);
+    // 5. per-trace energies
     block_sum2<THREADS>(ea, eb, red);
     if (threadIdx.x == 0) {
       s.Epart[t0] = ea;
@@ -343,6 +402,30 @@ __global__ void window_kernel(SurveyDev s, const double* __restrict__ td, double
   s.L[t] = L;
 }
 
+// Band spectrum (Nw or its 16-bit embedding) of the current N field.
+template <int NT>
+__global__ void __launch_bounds__(threads_for(NT))
+spectrum_kernel(SurveyDev s) {
+  constexpr int THREADS = threads_for(NT);
+  extern __shared__ float4 smem_raw[];
+  float2* x = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = x + NT;
+  for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
+  __syncthreads();
+  const int npairs = (s.ncols + 1) / 2;
+  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+    const int t0 = 2 * p;
+    const bool hasb = t0 + 1 < s.ncols;
+    const int64_t ba = field_offset(s, t0);
+    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+    for (int j = threadIdx.x; j < NT; j += THREADS)
+      x[j] = make_float2(s.fN[ba + j], hasb ? s.fN[bb + j] : 0.f);
+    __syncthreads();
+    forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
+    __syncthreads();
+  }
+}
+
 __global__ void green_kernel(SurveyDev s, float* __restrict__ out) {
   const int64_t total = (int64_t)s.F * s.ns * s.nt;
   const int mask = s.nt - 1;
@@ -356,10 +439,22 @@ __global__ void green_kernel(SurveyDev s, float* __restrict__ out) {
 
 template <int NT>
 cudaError_t set_attrs() {
-  const int bytes = 2 * NT * (int)sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       3 * NT * (int)sizeof(float2));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NT * (int)sizeof(float2));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(spectrum_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              2 * NT * (int)sizeof(float2));
+}
+
+template <int NT>
+cudaError_t launch_spec_nt(const SurveyDev& s, cudaStream_t st, int num_sms) {
+  const int npairs = (s.ncols + 1) / 2;
+  int grid = num_sms * 4;
+  if (grid > npairs) grid = npairs;
+  spectrum_kernel<NT><<<grid, threads_for(NT), 2 * NT * sizeof(float2), st>>>(s);
+  return cudaGetLastError();
 }
 
 template <int NT>
@@ -368,7 +463,7 @@ cudaError_t launch_epi_nt(const SurveyDev& s, int odd, double* slot, cudaStream_
   const int per_sm = NT >= 4096 ? 2 : 4;
   int grid = num_sms * per_sm;
   if (grid > npairs) grid = npairs;
-  const size_t bytes = 2 * NT * sizeof(float2);
+  const size_t bytes = 3 * NT * sizeof(float2);
   epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, odd, slot);
   return cudaGetLastError();
 }
@@ -400,7 +495,8 @@ cudaError_t launch_init_nt(const SurveyDev& s, const float* Gd, cudaStream_t st,
   }
 
 cudaError_t prepare_kernels() {
-  cudaError_t e;
+  cudaError_t e = prepare_contract();
+  if (e != cudaSuccess) return e;
 #define MK_ATTR(N) \
   if ((e = set_attrs<N>()) != cudaSuccess) return e;
   MK_ATTR(32) MK_ATTR(64) MK_ATTR(128) MK_ATTR(256) MK_ATTR(512) MK_ATTR(1024) MK_ATTR(2048)
@@ -425,6 +521,12 @@ cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, in
 cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st) {
   window_kernel<<<(s.ncols + 255) / 256, 256, 0, st>>>(s, td, eps);
   return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const SurveyDev& s, cudaStream_t st, int num_sms) {
+#define MK_CALL(N) launch_spec_nt<N>(s, st, num_sms)
+  MK_NT_SWITCH(s.nt, MK_CALL)
+#undef MK_CALL
 }
 
 cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms) {

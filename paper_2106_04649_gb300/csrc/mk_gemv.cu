@@ -1,0 +1,356 @@
+// The contraction of Eq. (1) for one focal point: a complex GEMV per frequency,
+// S_m(k) = c * sum_r R_m(k, r) Nw_m(r), bound by HBM bandwidth.
+//
+// Paper, Implementation section: the space integral over the fastest axis of
+// R is a segmented dot product (pointwise product followed by a segmented
+// reduction, one segment per shot).  Here the product and the reduction are
+// one pass: R is read from HBM exactly once per iteration, the field
+// spectrum stays on chip, and a warp-shuffle tree reduces each row.
+//
+// Main kernel (gemv_bulk_kernel): each CTA (one per SM) owns a contiguous
+// range of rows (m, k) of the frequency-major R and streams it through a
+// ring of shared-memory stages filled by bulk asynchronous copies
+// (cp.async.bulk + mbarrier), so that ~190 KB per SM are in flight; one
+// producer lane issues the copies, eight consumer warps each reduce one row
+// per stage with 128-bit shared loads, their slice of Nw_m held in registers
+// (reloaded only when m changes), and a warp-shuffle tree.  Every wait is
+// bounded: on time-out the kernel drains its copies, sets an error word and
+// returns.  Rows too long for the ring use the register-streaming kernels.
+
+#include "mk_internal.h"
+
+namespace mk {
+namespace {
+
+__device__ __forceinline__ float4 ld_stream(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
+// Rows of RQ float4 (two complex each); lane l owns float4 l, l + 32, ...
+template <int PER>
+__global__ void __launch_bounds__(256)
+gemv_c64_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S,
+                int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t row0 = warp * total_rows / nwarps;
+  const int64_t row1 = (warp + 1) * total_rows / nwarps;
+  int cur_w = -1;
+  float4 nv[PER];
+  for (int64_t row = row0; row < row1; ++row) {
+    const int w = (int)(row / ns);
+    const int k = (int)(row - (int64_t)w * ns);
+    if (w != cur_w) {
+      const float4* nrow = Nw + (int64_t)w * nw_stride4;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int i = lane + 32 * q;
+        nv[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      cur_w = w;
+    }
+    const float4* rrow = R + row * rq;
+    float4 rv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int i = lane + 32 * q;
+      rv[q] = i < rq ? ld_stream(rrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float re = 0.f, im = 0.f;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      re = fmaf(rv[q].x, nv[q].x, re);
+      re = fmaf(-rv[q].y, nv[q].y, re);
+      re = fmaf(rv[q].z, nv[q].z, re);
+      re = fmaf(-rv[q].w, nv[q].w, re);
+      im = fmaf(rv[q].x, nv[q].y, im);
+      im = fmaf(rv[q].y, nv[q].x, im);
+      im = fmaf(rv[q].z, nv[q].w, im);
+      im = fmaf(rv[q].w, nv[q].z, im);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+  }
+}
+
+// Rows longer than the register-resident form: Nw is re-read through L1.
+__global__ void __launch_bounds__(256)
+gemv_c64_long_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S,
+                     int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t row0 = warp * total_rows / nwarps;
+  const int64_t row1 = (warp + 1) * total_rows / nwarps;
+  for (int64_t row = row0; row < row1; ++row) {
+    const int w = (int)(row / ns);
+    const int k = (int)(row - (int64_t)w * ns);
+    const float4* nrow = Nw + (int64_t)w * nw_stride4;
+    const float4* rrow = R + row * rq;
+    float re = 0.f, im = 0.f;
+    for (int base = 0; base < rq; base += 32 * 8) {
+      float4 rv[8], nv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int i = base + lane + 32 * q;
+        rv[q] = i < rq ? ld_stream(rrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        nv[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        re = fmaf(rv[q].x, nv[q].x, re);
+        re = fmaf(-rv[q].y, nv[q].y, re);
+        re = fmaf(rv[q].z, nv[q].z, re);
+        re = fmaf(-rv[q].w, nv[q].w, re);
+        im = fmaf(rv[q].x, nv[q].y, im);
+        im = fmaf(rv[q].y, nv[q].x, im);
+        im = fmaf(rv[q].z, nv[q].w, im);
+        im = fmaf(rv[q].w, nv[q].z, im);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+  }
+}
+
+// ---------------------------------------------------------------- bulk-copy ring
+constexpr int kConsWarps = 8;                       // consumer warps = rows per stage
+constexpr int kBulkThreads = (kConsWarps + 1) * 32;  // + one producer warp
+constexpr int kMaxStages = 8;
+constexpr int kRingBytes = 200 * 1024;
+constexpr uint32_t kSpinLimit = 1u << 24;  // bounded mbarrier polls (seconds at worst)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+template <int PER>
+__global__ void __launch_bounds__(kBulkThreads, 1)
+gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S, int ns,
+                 int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows, int stages,
+                 int* __restrict__ err) {
+  extern __shared__ __align__(128) float4 ring[];
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * total_rows / gridDim.x;
+  const int64_t row1 = (int64_t)(blockIdx.x + 1) * total_rows / gridDim.x;
+  const int64_t ngroups = (row1 - row0 + kConsWarps - 1) / kConsWarps;
+  const int stage_f4 = kConsWarps * rq;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), kConsWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kConsWarps) {  // producer: one lane issues the bulk copies
+    if (lane == 0) {
+      bool ok = true;
+      int64_t g = 0;
+      for (; g < ngroups; ++g) {
+        const int s = (int)(g % stages);
+        const uint32_t ph = (uint32_t)((g / stages) & 1);
+        if (!mbar_wait_bounded(smem_u32(&empty_bar[s]), ph ^ 1u)) {
+          ok = false;
+          break;
+        }
+        const int64_t r = row0 + g * kConsWarps;
+        const int64_t left = row1 - r;
+        const int nrows = left < kConsWarps ? (int)left : kConsWarps;
+        const uint32_t bytes = (uint32_t)nrows * (uint32_t)rq * 16u;
+        mbar_expect_tx(smem_u32(&full_bar[s]), bytes);
+        bulk_g2s(smem_u32(ring + (size_t)s * stage_f4), R + r * rq, bytes, smem_u32(&full_bar[s]));
+      }
+      // no copy may still be in flight when the CTA exits
+      for (int64_t q = (g > stages ? g - stages : 0); q < g; ++q) {
+        if (!mbar_wait_bounded(smem_u32(&full_bar[q % stages]), (uint32_t)((q / stages) & 1))) ok = false;
+      }
+      if (!ok && err) atomicExch(err, 1);
+    }
+    return;
+  }
+
+  // consumers: warp w reduces row w of every stage
+  int cur_w = -1;
+  float4 nv[PER];
+  for (int64_t g = 0; g < ngroups; ++g) {
+    const int s = (int)(g % stages);
+    const uint32_t ph = (uint32_t)((g / stages) & 1);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&full_bar[s]), ph));
+    if (!ok) {
+      if (lane == 0 && err) atomicExch(err, 2);
+      return;
+    }
+    const int64_t row = row0 + g * kConsWarps + warp;
+    if (row < row1) {
+      const int w = (int)(row / ns);
+      const int k = (int)(row - (int64_t)w * ns);
+      if (w != cur_w) {
+        const float4* nrow = Nw + (int64_t)w * nw_stride4;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+          const int i = lane + 32 * q;
+          nv[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cur_w = w;
+      }
+      const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int i = lane + 32 * q;
+        const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        re = fmaf(rv.x, nv[q].x, re);
+        re = fmaf(-rv.y, nv[q].y, re);
+        re = fmaf(rv.z, nv[q].z, re);
+        re = fmaf(-rv.w, nv[q].w, re);
+        im = fmaf(rv.x, nv[q].y, im);
+        im = fmaf(rv.y, nv[q].x, im);
+        im = fmaf(rv.z, nv[q].w, im);
+        im = fmaf(rv.w, nv[q].z, im);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+      }
+      if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+  }
+}
+
+int bulk_stages(int rq) {
+  const int stage_bytes = kConsWarps * rq * 16;
+  int st = kRingBytes / stage_bytes;
+  return st > kMaxStages ? kMaxStages : st;
+}
+
+template <int PER>
+cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
+  const int rq = s.r_pad / 2;
+  const int stages = bulk_stages(rq);
+  const size_t smem = (size_t)stages * kConsWarps * rq * 16;
+  const int64_t total = (int64_t)s.nw * s.ns;
+  int64_t grid = num_sms;
+  if (grid * kConsWarps > total) grid = (total + kConsWarps - 1) / kConsWarps;
+  gemv_bulk_kernel<PER><<<(unsigned)grid, kBulkThreads, smem, st>>>(
+      reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq,
+      s.nw_stride / 2, s.s_stride, s.c, total, stages, s.err);
+  return cudaGetLastError();
+}
+
+template <int PER>
+cudaError_t set_bulk_attr() {
+  return cudaFuncSetAttribute(gemv_bulk_kernel<PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+}
+
+template <int PER>
+cudaError_t launch_gemv_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemv_c64_kernel<PER>, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) occ = 1;
+  const int64_t total = (int64_t)s.nw * s.ns;
+  int64_t grid = (int64_t)num_sms * occ;
+  if (grid * 8 > total) grid = (total + 7) / 8;
+  gemv_c64_kernel<PER><<<(unsigned)grid, 256, 0, st>>>(
+      reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns,
+      s.r_pad / 2, s.nw_stride / 2, s.s_stride, s.c, total);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t prepare_gemv() {
+  cudaError_t e;
+#define MK_BULK_ATTR(P) \
+  if ((e = set_bulk_attr<P>()) != cudaSuccess) return e;
+  MK_BULK_ATTR(1) MK_BULK_ATTR(2) MK_BULK_ATTR(4) MK_BULK_ATTR(6) MK_BULK_ATTR(8) MK_BULK_ATTR(10) MK_BULK_ATTR(12)
+  MK_BULK_ATTR(16) MK_BULK_ATTR(20)
+#undef MK_BULK_ATTR
+  return cudaSuccess;
+}
+
+cudaError_t launch_gemv(const SurveyDev& s, cudaStream_t st, int num_sms) {
+  const int rq = s.r_pad / 2;
+  const int per = (rq + 31) / 32;
+  if (per <= 20 && bulk_stages(rq) >= 2) {
+    switch (per) {
+      case 1: return launch_bulk_per<1>(s, st, num_sms);
+      case 2: return launch_bulk_per<2>(s, st, num_sms);
+      case 3: case 4: return launch_bulk_per<4>(s, st, num_sms);
+      case 5: case 6: return launch_bulk_per<6>(s, st, num_sms);
+      case 7: case 8: return launch_bulk_per<8>(s, st, num_sms);
+      case 9: case 10: return launch_bulk_per<10>(s, st, num_sms);
+      case 11: case 12: return launch_bulk_per<12>(s, st, num_sms);
+      case 13: case 14: case 15: case 16: return launch_bulk_per<16>(s, st, num_sms);
+      default: return launch_bulk_per<20>(s, st, num_sms);
+    }
+  }
+  switch (per) {
+    case 1: return launch_gemv_per<1>(s, st, num_sms);
+    case 2: return launch_gemv_per<2>(s, st, num_sms);
+    case 3: case 4: return launch_gemv_per<4>(s, st, num_sms);
+    case 5: case 6: return launch_gemv_per<6>(s, st, num_sms);
+    case 7: case 8: return launch_gemv_per<8>(s, st, num_sms);
+    case 9: case 10: return launch_gemv_per<10>(s, st, num_sms);
+    case 11: case 12: return launch_gemv_per<12>(s, st, num_sms);
+    default: {
+      const int64_t total = (int64_t)s.nw * s.ns;
+      int64_t grid = (int64_t)num_sms * 8;
+      if (grid * 8 > total) grid = (total + 7) / 8;
+      gemv_c64_long_kernel<<<(unsigned)grid, 256, 0, st>>>(
+          reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq,
+          s.nw_stride / 2, s.s_stride, s.c, total);
+      return cudaGetLastError();
+    }
+  }
+}
+
+}  // namespace mk

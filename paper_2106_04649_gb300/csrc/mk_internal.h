@@ -26,6 +26,10 @@ struct SurveyDev {
   int rprec;       // mk_rprec
 
   const float2* R;  // [nw][ns][r_pad] complex FP32 (MK_R_C64)
+  const void* Rq0;  // 16-bit R [nw][ns][2 r_pad] (hi part for split BF16)
+  const void* Rq1;  // lo part of split BF16 R
+  void* Bq0;        // 16-bit field embedding [nw][2F][2 r_pad], hi part
+  void* Bq1;        // lo part
   float2* Nw;       // [nw][nw_stride]
   float2* S;        // [nw][s_stride]
   float* fN;        // [F][ns][nt] last N_i
@@ -39,16 +43,30 @@ struct SurveyDev {
   double* Epart;    // [ncols + 1] per-trace energies
   unsigned* counter;  // last-block counter of the epilogue
   const float2* tw;   // [nt] e^{-2 pi i q / nt}
+  int* err;           // device error word (bounded waits that ran out); may be null
 };
 
 // Kernel launchers (return the launch status; the caller checks it).
-cudaError_t launch_contract(const SurveyDev& s, cudaStream_t st, int num_sms, int* nlaunch);
+struct UmmaMaps;  // tensor maps of the tcgen05 contraction (mk_umma.cu)
+UmmaMaps* umma_create(const SurveyDev& s);
+void umma_destroy(UmmaMaps* mp);
+cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms);
+cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms, int* nlaunch);
+cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
+                               int num_sms);
 cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
                             int num_sms);
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);
+cudaError_t launch_spectrum(const SurveyDev& s, cudaStream_t st, int num_sms);  // band spectrum of the N field
+cudaError_t launch_load_rows(const float2* src, float2* dst, int64_t rows, int nrec, int r_pad, cudaStream_t st,
+                             int num_sms);
 cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st);
 cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms);
 cudaError_t prepare_kernels();  // one-time function attributes (large dynamic smem)
+cudaError_t prepare_contract();  // called by prepare_kernels
+cudaError_t prepare_gemv();
+cudaError_t launch_gemv(const SurveyDev& s, cudaStream_t st, int num_sms);
+cudaError_t launch_cgemm_simt(const SurveyDev& s, cudaStream_t st);
 void set_noplan_error(const char* msg);  // message returned by mk_last_error(NULL)
 
 }  // namespace mk

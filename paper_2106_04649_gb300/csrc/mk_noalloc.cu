@@ -170,7 +170,7 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
     return set_err(MK_ERR_CUDA, "init launch", cudaGetErrorString(e));
   for (int it = 0; it < niter; ++it) {
     int nl = 0;
-    if ((e = mk::launch_contract(v, stream, num_sms, &nl)) != cudaSuccess)
+    if ((e = mk::launch_contract(v, nullptr, stream, num_sms, &nl)) != cudaSuccess)
       return set_err(MK_ERR_CUDA, "contraction launch", cudaGetErrorString(e));
     double* es = energy ? energy + (size_t)it * v.F : slot;
     if ((e = mk::launch_epilogue(v, it & 1, es, stream, num_sms)) != cudaSuccess)

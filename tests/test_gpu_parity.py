@@ -157,3 +157,98 @@ def test_call_order_errors(tiny_inputs):
         B.mk_fetch_fields(p.handle, 5, N.MK_F_N, out.ctypes.data, out.nbytes, False)
     assert ei.value.status == N.MK_ERR_ARG
     p.close()
+
+
+@pytest.mark.parametrize("n", [200, 353, 500, 700, 1000, 1201, 1400])
+def test_contraction_row_lengths(n):
+    # every register/ring variant of the F = 1 contraction (row lengths 256 .. 1408 complex)
+    s = small_survey(n=n, nt=64, dt=0.008, nfocal=1, fmax_hz=8.0)
+    R, td, Gd = survey_inputs(s)
+    _, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 2, history=True)
+    p = _plan(s, R, Gd, td)
+    for i in range(2):
+        p.iterate(1)
+        _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"n={n} iter {i}")
+    p.close()
+
+
+def test_load_paths_agree(tiny_inputs):
+    # pageable host, pinned host (read in place by the load kernel) in out-of-order
+    # chunks, and device sources must give bit-identical runs
+    import torch
+    from paper_2106_04649_gb300.api import Plan
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    outs = []
+    for mode in ("pageable", "pinned", "device"):
+        p = Plan([desc_for(s)])
+        if mode == "pageable":
+            p.load_R(0, R)
+        elif mode == "pinned":
+            Rp = torch.from_numpy(R).pin_memory()
+            from paper_2106_04649_gb300 import binding as B
+            nw, n = R.shape[0], R.shape[1]
+            for a, b in [(200, nw), (0, 77), (77, 200)]:
+                B.mk_load_R(p.handle, 0, Rp.data_ptr() + a * n * n * 8, a, b - a, False)
+        else:
+            p.load_R(0, torch.from_numpy(R).cuda())
+        p.set_Gd_window(0, Gd, td, s.eps)
+        e = p.iterate(3)
+        outs.append((e, p.fetch_fields(0)))
+        p.close()
+    for e, f in outs[1:]:
+        assert np.array_equal(e, outs[0][0])
+        assert np.array_equal(f, outs[0][1])
+
+
+def test_paper_small_F64_sampled_focal_points():
+    # the 64-point line at full size; the oracle computes sampled focal points one by one
+    s = S.paper_small_survey(64)
+    R, td, Gd = survey_inputs(s)
+    p = _plan(s, R, Gd, td)
+    e = p.iterate(16)
+    f = p.fetch_fields(0)
+    p.close()
+    sel = [0, 17, 40, 63]
+    st = M.run(R.astype(np.complex128), Gd[sel].astype(np.float64), td[sel], s.eps, s.dt, s.dx, 16)
+    ref = _oracle_fields(st)
+    for i, name in enumerate(FIELD_NAMES):
+        err = rel_l2(f[i][sel], ref[i])
+        assert err <= TOL_N, f"F=64 {name}: rel L2 {err:.3e}"
+    eref = np.array(st.energy)
+    assert np.max(np.abs(e[:, sel] - eref) / eref) <= TOL_E
+
+
+def _state_array(st):
+    return np.stack([st.N, st.f1plus, st.f1min, st.f2p, st.pmin]).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", ["tiny", "paper-small-F4"])
+def test_per_iteration_from_identical_inputs(case, tiny_inputs):
+    # one synthesis + epilogue from the oracle's own (FP32-rounded) state: <= 1e-5 per iteration
+    if case == "tiny":
+        s, R64, td, Gd64 = tiny_inputs
+        R = R64.astype(np.complex64)
+        Gd = Gd64.astype(np.float32)
+        niter = 16
+    else:
+        s = S.paper_small_survey(64)
+        sel = [0, 21, 42, 63]
+        s.focal = s.focal[sel]
+        R, td, Gd = survey_inputs(s)
+        niter = 6
+    st0 = M.initialise(Gd.astype(np.float64))
+    _, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, niter, history=True)
+    p = _plan(s, R, Gd, td)
+    prev = st0
+    for i in range(niter):
+        p.set_fields(0, _state_array(prev), i)
+        p.iterate(1)
+        f = p.fetch_fields(0)
+        ref = _oracle_fields(hist[i])
+        for j, name in enumerate(FIELD_NAMES):
+            err = rel_l2(f[j], ref[j])
+            assert err <= TOL_ITER, f"{case} iter {i} {name}: {err:.3e}"
+        prev = hist[i]
+    p.close()
