@@ -3,15 +3,18 @@
 One step = one full pass of the hot path for one set of focal points: the
 initialisation (first arrivals, windows, spectrum of N_{-1}) and 16 Neumann
 iterations (contraction, inverse transform, reversal, mute, accumulation,
-forward transform), all in libmarchenko.so kernels.  The default workload is
+forward transform), all in libmarchenko.so kernels.  The headline workload is
 the paper-small survey: 601 x 601 positions at dx = 10 m, nt = 2048,
 dt = 4 ms, R band-limited to 0-60 Hz (492 bins, complex FP32, 1.42 GB
-resident in HBM), one focal point (--nfocal 64 for the 64-point line).
+resident in HBM), one focal point.  The same run also measures variants of
+that survey (64 focal points, 601 focal points, tensor-core precisions) and
+reports them under "variants".
 
 Metric: focal points per second to convergence (16 iterations), with the
 contraction's HBM bandwidth and FLOP rate against the measured roofline.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--nfocal F] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--nfocal 1|64|601]
+                    [--rprec c64|cbf16|cf16|split|split3] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle on the host cores (the slow
 baseline) on the same workload, on a bounded sample of focal points.
@@ -28,7 +31,6 @@ import os
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -37,33 +39,45 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NITER = 16
-L2_NOTE = "inputs larger than L2: R (1.42 GB) is streamed from HBM every iteration"
+L2_NOTE = "inputs larger than L2: R (0.71-2.1 GB) is streamed from HBM every iteration"
+RPREC = {"c64": 0, "cbf16": 1, "cf16": 2, "split": 3, "split3": 4}
+NPROD = {1: 2, 2: 2, 3: 3, 4: 6}  # tensor-core products per complex MAC, per 16-bit form
+RBYTES = {"c64": 8, "cbf16": 4, "cf16": 4, "split": 8, "split3": 12}  # stored bytes per complex R value
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--nfocal", type=int, default=1, choices=[1, 64])
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--nfocal", type=int, default=1, choices=[1, 64, 601])
+    ap.add_argument("--rprec", default="c64", choices=list(RPREC))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--no-variants", action="store_true", help="measure the headline workload only")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
-def survey(nfocal):
+def survey(nfocal, world=1, rank=0):
+    """The paper-small survey with nfocal focal points; with several ranks each
+    rank takes its own nfocal points of a line of world * nfocal points."""
     import synthetic as S
-    return S.paper_small_survey(nfocal)
+    s = S.paper_small_survey(nfocal)
+    if world > 1:
+        line = S.focal_line(s.n, s.dx, world * nfocal, 1200.0)
+        s.focal = S.focal_shard(line, world, rank)
+    return s
 
 
-def workload_config(s, nfocal):
+def workload_config(s, nfocal, rprec):
     return {
         "workload": f"paper-small: {s.n}x{s.n} sources/receivers, dx={s.dx:g} m, nt={s.nt}, dt={s.dt * 1e3:g} ms, "
-                    f"R band 0-60 Hz ({s.nw} bins) complex FP32 resident, {nfocal} focal point(s) at z=1200 m, "
+                    f"R band 0-60 Hz ({s.nw} bins) resident as {rprec}, {nfocal} focal point(s) at z=1200 m, "
                     f"{NITER} Neumann iterations",
-        "nsrc": s.n, "nrec": s.n, "nt": s.nt, "nw": s.nw, "nfocal": nfocal, "niter": NITER, "rprec": "c64",
+        "nsrc": s.n, "nrec": s.n, "nt": s.nt, "nw": s.nw, "nfocal": nfocal, "niter": NITER, "rprec": rprec,
         "l2": L2_NOTE,
     }
 
@@ -120,8 +134,8 @@ def measured_peaks():
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return d.get("hbm_gbs", 6800.0), "measured"
-    return 6800.0, "fallback"
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
 def kernel_source_hash(src: str) -> str:
@@ -141,6 +155,35 @@ def profiled_traffic(workload_key: str):
     if not e or e.get("source_sha256_16") != kernel_source_hash(e.get("source", "")):
         return None
     return e.get("dram_bytes_per_launch")
+
+
+def roofline_for(s, F, rprec, c_ms):
+    """Roofline object of the dominant kernel (the contraction) from its mean launch time."""
+    peaks, kind = measured_peaks()
+    n_w, n = s.nw, s.n
+    flops = 8.0 * n_w * n * n * F
+    key = f"paper-small-F{F}-{rprec}"
+    if rprec == "c64" and F == 1:
+        b = n_w * n * n * 8 + 2 * n_w * n * 8
+        ach = b / (c_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": profiled_traffic(key),
+                "kernel": "gemv_bulk_kernel (complex GEMV)", "peak_source": f"{kind} hbm_gbs (copy)",
+                "algorithmic_bytes_per_launch": b, "algorithmic_flops_per_launch": flops, "avg_launch_ms": c_ms}
+    if rprec == "c64":
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        ach = flops / (c_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": profiled_traffic(key), "kernel": "cgemm_f32_kernel (SIMT FP32 complex GEMM)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "algorithmic_flops_per_launch": flops, "avg_launch_ms": c_ms}
+    tflops = NPROD[RPREC[rprec]] * flops
+    peak = peaks["bf16_tflops_sustained"]
+    ach = tflops / (c_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": profiled_traffic(key), "kernel": f"umma_cgemm_kernel (tcgen05, {rprec}, "
+            f"{NPROD[RPREC[rprec]]} products)", "peak_source": f"{kind} bf16_tflops_sustained (cuBLAS)",
+            "algorithmic_flops_per_launch": tflops, "avg_launch_ms": c_ms}
 
 
 # --------------------------------------------------------------------------- CPU oracle
@@ -164,7 +207,7 @@ def cpu_worker(spec: str):
 
 def run_cpu_oracle(nfocal: int, reps: int):
     cores = os.cpu_count() or 1
-    sample = [0] if nfocal == 1 else [0, 21, 42, 63][: max(1, min(4, nfocal))]
+    sample = [0] if nfocal == 1 else [0, nfocal // 3, (2 * nfocal) // 3, nfocal - 1]
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
@@ -184,17 +227,19 @@ def main_reference(args):
         return
     s = survey(args.nfocal)
     reps = args.warmup + args.steps
+    if args.nfocal > 1:
+        reps = min(reps, 3 + max(1, args.warmup // 5))
     out, cores, sample = run_cpu_oracle(args.nfocal, reps)
-    times = out["times"][args.warmup:]
+    times = out["times"][min(args.warmup, len(out["times"]) - 1):]
     total = float(sum(times))
     value = out["focal_per_rep"] * len(times) / total
     line = {
         "impl": "reference",
         "metric": "focal points/sec to convergence (16 Neumann iterations)",
-        "value": value, "unit": "focal points/s", "n_gpus": args.gpus, "steps": args.steps,
+        "value": value, "unit": "focal points/s", "n_gpus": args.gpus, "steps": len(times),
         "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(s, args.nfocal),
+        "config": workload_config(s, args.nfocal, args.rprec),
         "cpu_baseline": {"value": value, "unit": "focal points/s", "cores": cores, "kind": "oracle",
                          "sample": f"focal points {sample} of {args.nfocal}, {NITER} iterations per step, "
                                    f"FP64 NumPy oracle, {cores} BLAS threads"},
@@ -204,6 +249,76 @@ def main_reference(args):
 
 
 # --------------------------------------------------------------------------- our arm
+class Runner:
+    """One plan on one workload; device-resident inputs; timed steps."""
+
+    def __init__(self, s, R, F, rprec, dev, local, timing=True):
+        import torch
+        import synthetic as S
+        from paper_2106_04649_gb300.api import Desc, Plan
+        from paper_2106_04649_gb300 import _native as N
+        self.s, self.F, self.rprec = s, F, rprec
+        self.td = S.survey_td(s)
+        self.Gd = S.gd_traces(s, self.td, np.float32)
+        flags = N.MK_FLAG_TIMING if timing else 0
+        self.desc = Desc(s.n, s.n, s.nt, F, s.dt, s.dx, s.fmax_hz, RPREC[rprec], flags)
+        self.stream = torch.cuda.current_stream(dev)
+        self.plan = Plan([self.desc], device=local, stream=self.stream)
+        Rd = torch.from_numpy(R).to(dev)
+        self.plan.load_R(0, Rd)
+        torch.cuda.synchronize()
+        del Rd
+        torch.cuda.empty_cache()
+        self.Gdd = torch.from_numpy(self.Gd).to(dev)
+        self.tdd = torch.from_numpy(self.td).to(dev)
+
+    def step(self):
+        self.plan.set_Gd_window(0, self.Gdd, self.tdd, self.s.eps)
+        self.plan.iterate(NITER, energy=False)
+
+    def timed(self, steps, warmup, clocks=None, dist=None):
+        import torch
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize()
+        self.plan.stats(reset=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks is not None:
+            clocks.start()
+            time.sleep(0.3)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(self.stream)
+        for _ in range(steps):
+            self.step()
+        ev1.record(self.stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        clk = clocks.stop() if clocks is not None else None
+        st = self.plan.stats(reset=True)
+        return ms, st, clk
+
+    def close(self):
+        self.plan.close()
+
+
+def summarize(s, F, rprec, ms, steps, st, world=1):
+    c_ms = st["contract_ms"] / max(1, st["contract_timed"])
+    e_ms = st["epilogue_ms"] / max(1, st["epilogue_timed"])
+    flops = 8.0 * s.nw * s.n * s.n * F
+    return {
+        "value": world * F * steps / (ms / 1e3), "ms_per_step": ms / steps,
+        "roofline": roofline_for(s, F, rprec, c_ms),
+        "synthesis": {"algorithmic_tflops": flops / (c_ms * 1e-3) / 1e12,
+                      "hbm_gbs_R": s.nw * s.n * s.n * RBYTES[rprec] / (c_ms * 1e-3) / 1e9,
+                      "contract_ms": c_ms, "epilogue_ms": e_ms,
+                      "share_contract": st["contract_ms"] / max(1e-9, ms)},
+        "gpu_launches": int(st["launches"]),
+    }
+
+
 def main_ours(args):
     import torch
     import torch.distributed as dist
@@ -214,102 +329,50 @@ def main_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
 
     import synthetic as S
-    from paper_2106_04649_gb300.api import Desc, Plan
     from paper_2106_04649_gb300 import _native as N
+    from paper_2106_04649_gb300 import binding as B
 
-    s = survey(args.nfocal)
+    s = survey(args.nfocal, world, rank)
     F = s.nfocal
-    R = S.reflection_band(s, dtype=np.complex64)
-    td = S.survey_td(s)
-    Gd = S.gd_traces(s, td, np.float32)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    desc = Desc(s.n, s.n, s.nt, F, s.dt, s.dx, s.fmax_hz, N.MK_R_C64, N.MK_FLAG_TIMING)
-    plan = Plan([desc], device=local, stream=stream)
-    Rd = torch.from_numpy(R).to(dev)
-    Gdd = torch.from_numpy(Gd).to(dev)
-    tdd = torch.from_numpy(td).to(dev)
-    plan.load_R(0, Rd)
-    torch.cuda.synchronize()
-    del Rd
-    torch.cuda.empty_cache()
-
-    def step():
-        plan.set_Gd_window(0, Gdd, tdd, s.eps)
-        plan.iterate(NITER, energy=False)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    plan.stats(reset=True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
-    st = plan.stats(reset=True)
+    R = S.reflection_band(s, dtype=np.complex64)  # the same R serves every focal set of this survey
+    run = Runner(s, R, F, args.rprec, dev, local)
+    ms, st, clk = run.timed(args.steps, args.warmup, ClockSampler(local), dist if world > 1 else None)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
         dist.barrier()
-    ms_per_step = ms / args.steps
-    value = world * F * args.steps / (ms / 1e3)
-
-    # roofline of the dominant kernel (the contraction)
-    n_w, n = s.nw, s.n
-    bytes_launch = n_w * n * n * 8 + n_w * n * F * 8 + n_w * n * F * 8
-    flops_launch = 8 * n_w * n * n * F
-    c_ms = st["contract_ms"] / max(1, st["contract_timed"])
-    e_ms = st["epilogue_ms"] / max(1, st["epilogue_timed"])
-    peak, peak_kind = measured_peaks()
-    achieved = bytes_launch / (c_ms * 1e-3) / 1e9
-    key = f"paper-small-F{F}"
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(key), "kernel": "contraction (complex GEMV, F=1)" if F == 1 else
-                "contraction (complex GEMM)", "peak_source": f"{peak_kind} hbm_gbs (copy)",
-                "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": c_ms}
-    synthesis = {"hbm_gbs": achieved, "tflops": flops_launch / (c_ms * 1e-3) / 1e12,
-                 "contract_ms": c_ms, "epilogue_ms": e_ms,
-                 "share_contract": st["contract_ms"] / max(1e-9, ms)}
+    head = summarize(s, F, args.rprec, ms, args.steps, st, world)
 
     # end to end through the C ABI with host buffers (R, G_d, t_d in; energies and G out)
     e2e = None
     if not args.no_e2e:
         Rh = torch.from_numpy(R).pin_memory()
-        Gh = torch.from_numpy(Gd).pin_memory()
-        th = torch.from_numpy(td).pin_memory()
-        from paper_2106_04649_gb300 import binding as B
-        Gout = torch.empty((1, F, n, s.nt), dtype=torch.float32).pin_memory()
+        Gh = torch.from_numpy(run.Gd).pin_memory()
+        th = torch.from_numpy(run.td).pin_memory()
+        Gout = torch.empty((1, F, s.n, s.nt), dtype=torch.float32).pin_memory()
         energy = torch.empty((NITER, F), dtype=torch.float64).pin_memory()
-        h2d = R.nbytes + Gd.nbytes + td.nbytes
+        h2d = R.nbytes + run.Gd.nbytes + run.td.nbytes
         d2h = Gout.numel() * 4 + energy.numel() * 8
+        h = run.plan.handle
 
         def e2e_step():
-            B.mk_load_R(plan.handle, 0, Rh.data_ptr(), 0, s.nw, False)
-            B.mk_set_Gd_window(plan.handle, 0, Gh.data_ptr(), th.data_ptr(), s.eps, False)
-            B.mk_iterate(plan.handle, NITER, energy.data_ptr())
-            B.mk_fetch_fields(plan.handle, 0, N.MK_F_G, Gout.data_ptr(), Gout.numel() * 4, False)
+            B.mk_load_R(h, 0, Rh.data_ptr(), 0, s.nw, False)
+            B.mk_set_Gd_window(h, 0, Gh.data_ptr(), th.data_ptr(), s.eps, False)
+            B.mk_iterate(h, NITER, energy.data_ptr())
+            B.mk_fetch_fields(h, 0, N.MK_F_G, Gout.data_ptr(), Gout.numel() * 4, False)
 
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, min(args.warmup, 3))):
             e2e_step()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        ksteps = max(1, min(args.steps, 50))
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(ksteps):
             e2e_step()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
@@ -317,8 +380,28 @@ def main_ours(args):
             t = torch.tensor([el], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
-        e2e = {"value": world * F * args.steps / el, "unit": "focal points/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / args.steps}
+        e2e = {"value": world * F * ksteps / el, "unit": "focal points/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / ksteps, "steps": ksteps,
+               "path": "mk_load_R (pinned host, read in place by the load kernel) + mk_set_Gd_window (host) + "
+                       "mk_iterate(16, energies to host) + mk_fetch_fields(G to host)"}
+    run.close()
+
+    variants = []
+    if not args.no_variants and world == 1:
+        for (vf, vp, vsteps) in [(64, "c64", 10), (64, "split", 20), (64, "split3", 20), (64, "cbf16", 20),
+                                 (601, "split3", 5), (601, "split", 5), (601, "c64", 3)]:
+            vs = survey(vf)
+            vr = Runner(vs, R, vf, vp, dev, local)
+            vms, vst, _ = vr.timed(vsteps, 2)
+            vr.close()
+            d = summarize(vs, vf, vp, vms, vsteps, vst)
+            d.update({"nfocal": vf, "rprec": vp, "steps": vsteps})
+            variants.append(d)
+        by = {(v["nfocal"], v["rprec"]): v["value"] for v in variants}
+        for vf in (64, 601):
+            for vp in ("split", "split3", "cbf16"):
+                if (vf, vp) in by and (vf, "c64") in by:
+                    variants.append({"mixed_vs_plain": f"F={vf} {vp} / c64", "factor": by[(vf, vp)] / by[(vf, "c64")]})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -328,16 +411,15 @@ def main_ours(args):
                "sample": f"focal points {sample} of {F}, {NITER} iterations, FP64 NumPy oracle, best of 2, "
                          f"{cores} BLAS threads"}
 
-    plan.close()
     if rank == 0:
         line = {
             "metric": "focal points/sec to convergence (16 Neumann iterations)",
-            "value": value, "unit": "focal points/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(s, F) | {"parallelism": f"focal-point replicas x{world}"},
-            "roofline": roofline, "synthesis": synthesis, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(st["launches"]), "clocks": clk,
+            "value": head["value"], "unit": "focal points/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.rprec == "c64" else "bf16", "data": "synthetic",
+            "config": workload_config(s, F, args.rprec) | {"parallelism": f"focal-point replicas x{world}"},
+            "roofline": head["roofline"], "synthesis": head["synthesis"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": head["gpu_launches"], "clocks": clk, "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

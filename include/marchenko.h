@@ -82,7 +82,8 @@ typedef enum {
   MK_R_C64 = 0,        /* complex FP32                                        */
   MK_R_CBF16 = 1,      /* complex BF16 (tensor-core contraction)              */
   MK_R_CF16 = 2,       /* complex FP16 (tensor-core contraction)              */
-  MK_R_SPLIT_BF16 = 3  /* BF16 hi + BF16 lo parts (3-product tensor-core form) */
+  MK_R_SPLIT_BF16 = 3, /* BF16 hi + BF16 lo parts (3-product tensor-core form) */
+  MK_R_SPLIT3_BF16 = 4 /* BF16 hi + mid + lo parts (6-product form, FP32-like)  */
 } mk_rprec;
 
 /* Field selection bits for mk_fetch_fields (output order = bit order). */
@@ -187,7 +188,10 @@ mk_status mk_iterate(mk_plan_t plan, int32_t niter, double* energy);
 
 /*
  * mk_fetch_fields - copy selected fields of one survey out, in bit order of
- * mask, each float [nfocal][nsrc][nt] (MK_F_G is computed on the GPU).
+ * mask, each float [nfocal][nsrc][nt].  The iterations accumulate f1plus and
+ * f1min only; N_last, f2p, pmin and G are formed on the GPU when fetched
+ * (f2p = f1plus - f1min(-t); pmin = synthesis of f2p - N_last, one extra
+ * contraction; G = f2p(-t) + pmin), which is exact algebra of Algorithm 1.
  *   out: host (dst_on_device = 0) or device (1) buffer of out_bytes >=
  *        popcount(mask) * nfocal * nsrc * nt * 4.
  * Errors: MK_ERR_ARG, MK_ERR_STATE (G_d not set), MK_ERR_CUDA.
@@ -198,12 +202,14 @@ mk_status mk_fetch_fields(mk_plan_t plan, int32_t survey, uint32_t mask, float* 
 /*
  * mk_set_fields - resume a series from saved fields (checkpoint / restart;
  * the paper's GPU code keeps iRN on disk between iterations, Algorithm 1).
- * Overwrites the selected fields of one survey with caller data, sets the
- * iteration index (its parity decides f1min vs f1plus, Algorithm 1) and
- * recomputes the band spectrum of N from the (new) N field, so that the next
- * mk_iterate continues from exactly these fields.  Windows stay those of the
- * last mk_set_Gd_window.
- *   mask: MK_F_N | MK_F_F1P | MK_F_F1M | MK_F_F2P | MK_F_PMIN subset (not MK_F_G);
+ * Sets the state of one survey from caller data -- the last N, f1plus and
+ * f1min -- and the iteration index (its parity decides f1min vs f1plus,
+ * Algorithm 1), and recomputes the band spectrum of N, so that the next
+ * mk_iterate continues from exactly these fields.  f2p and pmin follow from
+ * the state (f2p = f1plus - f1min(-t), pmin = synthesis of f2p - N); if the
+ * mask includes them their data is skipped.  Windows stay those of the last
+ * mk_set_Gd_window.
+ *   mask: must contain MK_F_N | MK_F_F1P | MK_F_F1M; may add MK_F_F2P, MK_F_PMIN;
  *   in:   float [popcount(mask)][nfocal][nsrc][nt] in bit order, host or device.
  *   iteration: the number of iterations these fields represent (>= 0).
  * Errors: MK_ERR_ARG, MK_ERR_STATE (G_d not set), MK_ERR_CUDA.

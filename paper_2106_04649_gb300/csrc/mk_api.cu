@@ -30,6 +30,8 @@ struct Survey {
   int nloaded = 0;
   bool ready = false;
   int iter = 0;
+  bool n_in_field = true;   // fN holds the last N (else it follows from S)
+  bool derived_valid = false;  // f2p and pmin formed since the last change
   size_t offset = 0, bytes = 0;  // carving inside the workspace
 };
 
@@ -90,7 +92,7 @@ mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nt=%d must be a power of two in [32, 8192]", i, d.nt);
   if (!(d.dt > 0.0) || !(d.dx > 0.0) || !isfinite(d.dt) || !isfinite(d.dx))
     return fail(p, MK_ERR_ARG, "survey %d: dt and dx must be finite and > 0", i);
-  if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT_BF16)
+  if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT3_BF16)
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: unknown R storage precision %d", i, d.rprec);
   if ((int64_t)d.nsrc * d.nfocal > (int64_t)1 << 30)
     return fail(p, MK_ERR_ARG, "survey %d: nsrc * nfocal too large", i);
@@ -123,8 +125,8 @@ size_t layout(Survey& sv, char* base) {
   if (d.rprec == MK_R_C64) {
     v.R = reinterpret_cast<const float2*>(take((size_t)v.nw * v.ns * v.r_pad * sizeof(float2)));
     v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
-    v.Rq0 = v.Rq1 = nullptr;
-    v.Bq0 = v.Bq1 = nullptr;
+    v.Rq0 = v.Rq1 = v.Rq2 = nullptr;
+    v.Bq0 = v.Bq1 = v.Bq2 = nullptr;
   } else {
     // 16-bit interleaved complex rows of 2 r_pad values; field embedding [nw][2F][2 r_pad]
     const size_t rq = (size_t)v.nw * v.ns * 2 * v.r_pad * 2;
@@ -132,9 +134,11 @@ size_t layout(Survey& sv, char* base) {
     v.R = nullptr;
     v.Nw = nullptr;
     v.Rq0 = take(rq);
-    v.Rq1 = d.rprec == MK_R_SPLIT_BF16 ? take(rq) : nullptr;
+    v.Rq1 = d.rprec >= MK_R_SPLIT_BF16 ? take(rq) : nullptr;
+    v.Rq2 = d.rprec == MK_R_SPLIT3_BF16 ? take(rq) : nullptr;
     v.Bq0 = take(bq);
     v.Bq1 = take(bq);
+    v.Bq2 = d.rprec == MK_R_SPLIT3_BF16 ? take(bq) : nullptr;
   }
   v.S = reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)));
   v.fN = reinterpret_cast<float*>(take(field));
@@ -198,6 +202,43 @@ TimedPair* next_pair(mk_plan_t p, int kind) {
   TimedPair* tp = &p->events[p->next_event++];
   tp->kind = kind;
   return tp;
+}
+
+// Forms the fields Algorithm 1 accumulates but the hot loop does not (N_last,
+// f2p, pmin) from the accumulated ones, for a fetch:
+//   N_last = -theta s_last(-t) (inverse transform of the last synthesis S),
+//   f2p = f1plus - f1min(-t),  pmin = synthesis(f2p - N_last).
+// The pmin synthesis reuses the contraction; the band spectrum of N_last is
+// restored afterwards so the series continues unchanged.
+mk_status materialize(mk_plan_t p, Survey& sv, uint32_t mask) {
+  mk::SurveyDev& v = sv.dev;
+  const bool need_pmin = mask & (MK_F_PMIN | MK_F_G);
+  const bool need_f2p = need_pmin || (mask & MK_F_F2P);
+  const bool need_n = need_f2p || (mask & MK_F_N);
+  if (need_n && !sv.n_in_field) {
+    MK_CUDA(p, mk::launch_inverse(v, v.fN, 0, p->stream, p->num_sms));
+    p->stats.launches++;
+    p->stats.other_launches++;
+    sv.n_in_field = true;
+  }
+  if (!need_f2p || sv.derived_valid) return MK_OK;
+  MK_CUDA(p, mk::launch_f2p(v, v.scratch, p->stream, p->num_sms));  // f2p, and f2p - N into scratch
+  p->stats.launches++;
+  p->stats.other_launches++;
+  const size_t field = (size_t)v.F * v.ns * v.nt * sizeof(float);
+  if (sv.iter == 0) {
+    MK_CUDA(p, cudaMemsetAsync(v.pmin, 0, field, p->stream));
+  } else {
+    int nl = 0;
+    MK_CUDA(p, mk::launch_spectrum(v, v.scratch, p->stream, p->num_sms));
+    MK_CUDA(p, mk::launch_contract(v, sv.umma, p->stream, p->num_sms, &nl));
+    MK_CUDA(p, mk::launch_inverse(v, v.pmin, 1, p->stream, p->num_sms));
+    MK_CUDA(p, mk::launch_spectrum(v, v.fN, p->stream, p->num_sms));  // restore the spectrum of N_last
+    p->stats.launches += 3 + nl;
+    p->stats.other_launches += 3 + nl;
+  }
+  sv.derived_valid = true;
+  return MK_OK;
 }
 
 }  // namespace
@@ -400,6 +441,8 @@ mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const d
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   sv->ready = true;
   sv->iter = 0;
+  sv->n_in_field = true;
+  sv->derived_valid = false;
   return MK_OK;
 }
 
@@ -433,6 +476,8 @@ mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
         p->stats.launches++;
         p->stats.epilogue_launches++;
         sv.iter++;
+        sv.n_in_field = false;
+        sv.derived_valid = false;
       }
     }
     if (energy) {
@@ -466,6 +511,7 @@ mk_status mk_fetch_fields(mk_plan_t p, int32_t survey, uint32_t mask, float* out
   const size_t field = (size_t)v.F * v.ns * v.nt;
   const size_t need = (size_t)__builtin_popcount(mask) * field * sizeof(float);
   if (out_bytes < need) return fail(p, MK_ERR_ARG, "output of %zu bytes, %zu needed", out_bytes, need);
+  if ((st = materialize(p, *sv, mask)) != MK_OK) return st;
   const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   const float* src[6] = {v.fN, v.f1p, v.f1m, v.f2p, v.pmin, nullptr};
   float* o = out;
@@ -498,8 +544,9 @@ mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float*
   p->err[0] = 0;
   if ((st = ensure_device(p)) != MK_OK) return st;
   if (!in) return fail(p, MK_ERR_ARG, "null input pointer");
-  if (mask == 0 || (mask & ~(MK_F_N | MK_F_F1P | MK_F_F1M | MK_F_F2P | MK_F_PMIN)))
-    return fail(p, MK_ERR_ARG, "field mask 0x%x invalid (MK_F_G cannot be set)", mask);
+  const uint32_t state = MK_F_N | MK_F_F1P | MK_F_F1M;
+  if ((mask & state) != state || (mask & ~(state | MK_F_F2P | MK_F_PMIN)))
+    return fail(p, MK_ERR_ARG, "field mask 0x%x invalid: N, f1plus and f1min are required, G cannot be set", mask);
   if (iteration < 0) return fail(p, MK_ERR_ARG, "iteration < 0");
   if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
   const mk::SurveyDev& v = sv->dev;
@@ -507,18 +554,20 @@ mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float*
   const size_t need = (size_t)__builtin_popcount(mask) * field * sizeof(float);
   if (in_bytes < need) return fail(p, MK_ERR_ARG, "input of %zu bytes, %zu needed", in_bytes, need);
   const cudaMemcpyKind kind = src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  float* dst[5] = {v.fN, v.f1p, v.f1m, v.f2p, v.pmin};
+  float* dst[5] = {v.fN, v.f1p, v.f1m, nullptr, nullptr};  // f2p and pmin follow from these
   const float* q = in;
   for (int b = 0; b < 5; ++b) {
     if (!(mask & (1u << b))) continue;
-    MK_CUDA(p, cudaMemcpyAsync(dst[b], q, field * sizeof(float), kind, p->stream));
+    if (dst[b]) MK_CUDA(p, cudaMemcpyAsync(dst[b], q, field * sizeof(float), kind, p->stream));
     q += field;
   }
-  MK_CUDA(p, mk::launch_spectrum(v, p->stream, p->num_sms));
+  MK_CUDA(p, mk::launch_spectrum(v, v.fN, p->stream, p->num_sms));
   p->stats.launches++;
   p->stats.other_launches++;
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   sv->iter = iteration;
+  sv->n_in_field = true;
+  sv->derived_valid = false;
   return MK_OK;
 }
 

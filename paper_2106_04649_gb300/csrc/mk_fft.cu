@@ -2,12 +2,22 @@
 //
 //  * epilogue: inverse transform of the band-limited synthesis result
 //    (Theory: "reverse Fourier transform"; Implementation: "padding"), time
-//    reversal and sign flip, theta mute, accumulation of pmin, f2p, f1min /
-//    f1plus (Algorithm 1), FP64 energy, and the forward transform of N_i
+//    reversal and sign flip, theta mute, accumulation of f1min / f1plus
+//    (Algorithm 1), FP64 energy, and the forward transform of N_i
 //    restricted to the band for the next contraction;
-//  * init: N_{-1} = f1plus = f2p = G_d(-t), f1min = pmin = 0 and the band
-//    spectrum of N_{-1} (Theory: initialisation);
-//  * green: G(t) = f2p(-t) + pmin(t).
+//  * init: N_{-1} = f1plus = G_d(-t), f1min = 0 and the band spectrum of
+//    N_{-1} (Theory: initialisation);
+//  * fetch-time fields: N_i = -theta s_i(-t) from the last synthesis result,
+//    f2p = f1plus - f1min(-t), pmin = IDFT of a synthesis of f2p - N_last,
+//    G(t) = f2p(-t) + pmin(t).
+//
+// Only f1plus / f1min are accumulated per iteration.  Algorithm 1 also
+// accumulates f2p and pmin; both follow from the series exactly:
+//    f2p = N_{-1} + sum_i N_i = f1plus - f1min(-t)   (odd N_i go to f1plus,
+//          even N_i reversed and negated to f1min),
+//    pmin = sum_{i<n} synthesis(N_{i-1}) = synthesis(f2p - N_{n-1})  (linearity),
+// so they are formed when fetched, which removes two full-length
+// read-modify-writes per trace and iteration from the hot loop.
 //
 // Two real traces share one complex transform (a + i b): the inverse
 // transform of X + iY with Hermitian X, Y gives x + iy; the forward transform
@@ -181,16 +191,27 @@ __device__ __forceinline__ float round16(float a) {
 template <bool BF16>
 __device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int t, float nr, float ni) {
   const int f = t % s.F, k = t / s.F;
-  const float hr = round16<BF16>(nr), hi = round16<BF16>(ni);
-  const float lr = nr - hr, li = ni - hi;
   const int64_t kp = 2 * (int64_t)s.r_pad;
   const int64_t e0 = ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k;
   uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
   uint32_t* b1 = reinterpret_cast<uint32_t*>(s.Bq1);
+  const float hr = round16<BF16>(nr), hi = round16<BF16>(ni);
+  float lr = nr - hr, li = ni - hi;  // exact in FP32
   b0[e0 >> 1] = pack2<BF16>(hr, -hi);
   b0[(e0 + kp) >> 1] = pack2<BF16>(hi, hr);
-  b1[e0 >> 1] = pack2<BF16>(lr, -li);
-  b1[(e0 + kp) >> 1] = pack2<BF16>(li, lr);
+  if (s.rprec == 4) {  // 3-way split: hi, mid = rn(x - hi), lo = rn(x - hi - mid)
+    const float mr = round16<BF16>(lr), mi = round16<BF16>(li);
+    b1[e0 >> 1] = pack2<BF16>(mr, -mi);
+    b1[(e0 + kp) >> 1] = pack2<BF16>(mi, mr);
+    lr -= mr;
+    li -= mi;
+    uint32_t* b2 = reinterpret_cast<uint32_t*>(s.Bq2);
+    b2[e0 >> 1] = pack2<BF16>(lr, -li);
+    b2[(e0 + kp) >> 1] = pack2<BF16>(li, lr);
+  } else {
+    b1[e0 >> 1] = pack2<BF16>(lr, -li);
+    b1[(e0 + kp) >> 1] = pack2<BF16>(li, lr);
+  }
 }
 
 // Forward transform of the pair held in x (a + i b), unpacked into the band
@@ -218,12 +239,40 @@ __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x,
   }
 }
 
+// Hermitian pack of the band spectra S[m][t0], S[m][t0 + 1] into
+// x = X + iY (bins outside the band zero; DC and Nyquist real).  All global
+// loads of a thread are issued before its shared-memory stores.
+template <int NT, int THREADS>
+__device__ __forceinline__ void pack_pair(const SurveyDev& s, float2* x, int t0, bool hasb) {
+  constexpr int PM = (NT / 2 + THREADS) / THREADS;  // bins 0 .. NT/2 per thread
+  float4 v[PM];
+#pragma unroll
+  for (int q = 0; q < PM; ++q) {
+    const int m = threadIdx.x + q * THREADS;
+    v[q] = (m <= NT / 2 && m < s.nw)
+               ? __ldg(reinterpret_cast<const float4*>(s.S + (int64_t)m * s.s_stride + t0))
+               : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int q = 0; q < PM; ++q) {
+    const int m = threadIdx.x + q * THREADS;
+    if (m > NT / 2) continue;
+    float2 X = make_float2(v[q].x, v[q].y);
+    float2 Y = hasb ? make_float2(v[q].z, v[q].w) : make_float2(0.f, 0.f);
+    if (m == 0 || m == NT / 2) {
+      X.y = 0.f;
+      Y.y = 0.f;
+    }
+    x[m] = make_float2(X.x - Y.y, X.y + Y.x);
+    if (m > 0 && m < NT / 2) x[NT - m] = make_float2(X.x + Y.y, Y.x - X.y);
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(threads_for(NT), NT <= 2048 ? 2 : 1)
 epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
   constexpr int THREADS = threads_for(NT);
   constexpr int PJ = NT / THREADS;  // samples per thread
-  constexpr int CH = PJ < 4 ? PJ : 4;  // samples per batch of field loads
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);  // inverse transform
   float2* y = x + NT;                               // N_i pair for the forward transform
@@ -236,78 +285,46 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
 
   const int npairs = (s.ncols + 1) / 2;
   const float inv = s.inv_nt;
-  float* __restrict__ pmin = s.pmin;
-  float* __restrict__ fN = s.fN;
-  float* __restrict__ f2p = s.f2p;
   float* __restrict__ f1 = odd ? s.f1p : s.f1m;
   for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
     const int t0 = 2 * p;
     const bool hasb = t0 + 1 < s.ncols;
     // 1. Hermitian pack of the two band spectra (bins outside the band are zero)
-    for (int m = threadIdx.x; m <= NT / 2; m += THREADS) {
-      float2 X = make_float2(0.f, 0.f), Y = make_float2(0.f, 0.f);
-      if (m < s.nw) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(s.S + (int64_t)m * s.s_stride + t0));
-        X = make_float2(v.x, v.y);
-        if (hasb) Y = make_float2(v.z, v.w);
-      }
-      if (m == 0 || m == NT / 2) {
-        X.y = 0.f;
-        Y.y = 0.f;
-      }
-      x[m] = make_float2(X.x - Y.y, X.y + Y.x);
-      if (m > 0 && m < NT / 2) x[NT - m] = make_float2(X.x + Y.y, Y.x - X.y);
-    }
+    pack_pair<NT, THREADS>(s, x, t0, hasb);
     __syncthreads();
     // 2. inverse transform: x[j] = nt * (s_a(j) + i s_b(j))
     fft_smem<NT, THREADS, true>(x, tw);
-    // 3. reverse, negate, mute, accumulate; N_i into y.  Field loads of a
-    //    batch of samples are issued before its stores (distinct arrays).
+    // 3. reverse, negate, mute; accumulate f1 (window samples only); N_i into y
     const int La = s.L[t0];
     const int Lb = hasb ? s.L[t0 + 1] : 0;
     const int64_t ba = field_offset(s, t0);
     const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
     double ea = 0.0, eb = 0.0;
+    float ha[PJ], hb[PJ];
 #pragma unroll
-    for (int q0 = 0; q0 < PJ; q0 += CH) {
-      float pa[CH], pb[CH], ga[CH], gb[CH], ha[CH], hb[CH];
+    for (int q = 0; q < PJ; ++q) {  // all loads first: one round trip
+      const int j = threadIdx.x + q * THREADS;
+      const int d = j < NT - j ? j : NT - j;
+      ha[q] = d < La ? f1[ba + j] : 0.f;
+      hb[q] = (hasb && d < Lb) ? f1[bb + j] : 0.f;
+    }
 #pragma unroll
-      for (int q = 0; q < CH; ++q) {
-        const int j = threadIdx.x + (q0 + q) * THREADS;
-        const int d = j < NT - j ? j : NT - j;
-        pa[q] = pmin[ba + j];
-        ga[q] = d < La ? f2p[ba + j] : 0.f;
-        ha[q] = d < La ? f1[ba + j] : 0.f;
-        pb[q] = hasb ? pmin[bb + j] : 0.f;
-        gb[q] = (hasb && d < Lb) ? f2p[bb + j] : 0.f;
-        hb[q] = (hasb && d < Lb) ? f1[bb + j] : 0.f;
+    for (int q = 0; q < PJ; ++q) {
+      const int j = threadIdx.x + q * THREADS;
+      const int d = j < NT - j ? j : NT - j;  // |signed index|
+      const float2 zj = x[j];
+      const float2 zr = x[(NT - j) & (NT - 1)];
+      const float sa = zj.x * inv, sb = zj.y * inv;
+      const float na = d < La ? -(zr.x * inv) : 0.f;
+      const float nb = d < Lb ? -(zr.y * inv) : 0.f;
+      y[j] = make_float2(na, nb);
+      if (d < La) {
+        f1[ba + j] = ha[q] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
+        ea += (double)na * (double)na;
       }
-#pragma unroll
-      for (int q = 0; q < CH; ++q) {
-        const int j = threadIdx.x + (q0 + q) * THREADS;
-        const int d = j < NT - j ? j : NT - j;  // |signed index|
-        const float2 zj = x[j];
-        const float2 zr = x[(NT - j) & (NT - 1)];
-        const float sa = zj.x * inv, sb = zj.y * inv;
-        const float na = d < La ? -(zr.x * inv) : 0.f;
-        const float nb = d < Lb ? -(zr.y * inv) : 0.f;
-        y[j] = make_float2(na, nb);
-        pmin[ba + j] = pa[q] + sa;
-        fN[ba + j] = na;
-        if (d < La) {
-          f2p[ba + j] = ga[q] + na;
-          f1[ba + j] = ha[q] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
-          ea += (double)na * (double)na;
-        }
-        if (hasb) {
-          pmin[bb + j] = pb[q] + sb;
-          fN[bb + j] = nb;
-          if (d < Lb) {
-            f2p[bb + j] = gb[q] + nb;
-            f1[bb + j] = hb[q] + (odd ? nb : sb);
-            eb += (double)nb * (double)nb;
-          }
-        }
+      if (d < Lb) {
+        f1[bb + j] = hb[q] + (odd ? nb : sb);
+        eb += (double)nb * (double)nb;
       }
     }
     __syncthreads();
@@ -364,15 +381,11 @@ init_kernel(SurveyDev s, const float* __restrict__ Gd) {
       x[j] = make_float2(na, nb);
       s.fN[ba + j] = na;
       s.f1p[ba + j] = na;
-      s.f2p[ba + j] = na;
       s.f1m[ba + j] = 0.f;
-      s.pmin[ba + j] = 0.f;
       if (hasb) {
         s.fN[bb + j] = nb;
         s.f1p[bb + j] = nb;
-        s.f2p[bb + j] = nb;
         s.f1m[bb + j] = 0.f;
-        s.pmin[bb + j] = 0.f;
       }
     }
     __syncthreads();
@@ -402,10 +415,10 @@ __global__ void window_kernel(SurveyDev s, const double* __restrict__ td, double
   s.L[t] = L;
 }
 
-// Band spectrum (Nw or its 16-bit embedding) of the current N field.
+// Band spectrum (Nw or its 16-bit embedding) of a field [F][ns][nt].
 template <int NT>
 __global__ void __launch_bounds__(threads_for(NT))
-spectrum_kernel(SurveyDev s) {
+spectrum_kernel(SurveyDev s, const float* __restrict__ src) {
   constexpr int THREADS = threads_for(NT);
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);
@@ -419,10 +432,66 @@ spectrum_kernel(SurveyDev s) {
     const int64_t ba = field_offset(s, t0);
     const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
     for (int j = threadIdx.x; j < NT; j += THREADS)
-      x[j] = make_float2(s.fN[ba + j], hasb ? s.fN[bb + j] : 0.f);
+      x[j] = make_float2(src[ba + j], hasb ? src[bb + j] : 0.f);
     __syncthreads();
     forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
     __syncthreads();
+  }
+}
+
+// Inverse transform of the band spectra in S, per trace:
+//   mode 0: dst = N = -theta s(-t) (the N_i of the last synthesis),
+//   mode 1: dst = s (a plain synthesis result, e.g. pmin).
+template <int NT>
+__global__ void __launch_bounds__(threads_for(NT))
+inverse_kernel(SurveyDev s, float* __restrict__ dst, int mode) {
+  constexpr int THREADS = threads_for(NT);
+  extern __shared__ float4 smem_raw[];
+  float2* x = reinterpret_cast<float2*>(smem_raw);
+  float2* tw = x + NT;
+  for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
+  __syncthreads();
+  const int npairs = (s.ncols + 1) / 2;
+  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
+    const int t0 = 2 * p;
+    const bool hasb = t0 + 1 < s.ncols;
+    pack_pair<NT, THREADS>(s, x, t0, hasb);
+    __syncthreads();
+    fft_smem<NT, THREADS, true>(x, tw);
+    const int La = s.L[t0];
+    const int Lb = hasb ? s.L[t0 + 1] : 0;
+    const int64_t ba = field_offset(s, t0);
+    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+    for (int j = threadIdx.x; j < NT; j += THREADS) {
+      float va, vb;
+      if (mode == 0) {
+        const int d = j < NT - j ? j : NT - j;
+        const float2 zr = x[(NT - j) & (NT - 1)];
+        va = d < La ? -(zr.x * s.inv_nt) : 0.f;
+        vb = d < Lb ? -(zr.y * s.inv_nt) : 0.f;
+      } else {
+        const float2 z = x[j];
+        va = z.x * s.inv_nt;
+        vb = z.y * s.inv_nt;
+      }
+      dst[ba + j] = va;
+      if (hasb) dst[bb + j] = vb;
+    }
+    __syncthreads();
+  }
+}
+
+// f2p = f1plus - f1min(-t); diff = f2p - N (input of the pmin synthesis).
+__global__ void f2p_kernel(SurveyDev s, float* __restrict__ diff) {
+  const int64_t total = (int64_t)s.F * s.ns * s.nt;
+  const int mask = s.nt - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i & mask);
+    const int64_t base = i - j;
+    const float v = s.f1p[i] - s.f1m[base + ((s.nt - j) & mask)];
+    s.f2p[i] = v;
+    diff[i] = v - s.fN[i];
   }
 }
 
@@ -444,16 +513,28 @@ cudaError_t set_attrs() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NT * (int)sizeof(float2));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(spectrum_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(spectrum_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           2 * NT * (int)sizeof(float2));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(inverse_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               2 * NT * (int)sizeof(float2));
 }
 
 template <int NT>
-cudaError_t launch_spec_nt(const SurveyDev& s, cudaStream_t st, int num_sms) {
+cudaError_t launch_inv_nt(const SurveyDev& s, float* dst, int mode, cudaStream_t st, int num_sms) {
   const int npairs = (s.ncols + 1) / 2;
   int grid = num_sms * 4;
   if (grid > npairs) grid = npairs;
-  spectrum_kernel<NT><<<grid, threads_for(NT), 2 * NT * sizeof(float2), st>>>(s);
+  inverse_kernel<NT><<<grid, threads_for(NT), 2 * NT * sizeof(float2), st>>>(s, dst, mode);
+  return cudaGetLastError();
+}
+
+template <int NT>
+cudaError_t launch_spec_nt(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms) {
+  const int npairs = (s.ncols + 1) / 2;
+  int grid = num_sms * 4;
+  if (grid > npairs) grid = npairs;
+  spectrum_kernel<NT><<<grid, threads_for(NT), 2 * NT * sizeof(float2), st>>>(s, src);
   return cudaGetLastError();
 }
 
@@ -523,10 +604,21 @@ cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_spectrum(const SurveyDev& s, cudaStream_t st, int num_sms) {
-#define MK_CALL(N) launch_spec_nt<N>(s, st, num_sms)
+cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms) {
+#define MK_CALL(N) launch_spec_nt<N>(s, src, st, num_sms)
   MK_NT_SWITCH(s.nt, MK_CALL)
 #undef MK_CALL
+}
+
+cudaError_t launch_inverse(const SurveyDev& s, float* dst, int mode, cudaStream_t st, int num_sms) {
+#define MK_CALL(N) launch_inv_nt<N>(s, dst, mode, st, num_sms)
+  MK_NT_SWITCH(s.nt, MK_CALL)
+#undef MK_CALL
+}
+
+cudaError_t launch_f2p(const SurveyDev& s, float* diff, cudaStream_t st, int num_sms) {
+  f2p_kernel<<<num_sms * 8, 256, 0, st>>>(s, diff);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms) {

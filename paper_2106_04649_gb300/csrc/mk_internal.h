@@ -26,10 +26,12 @@ struct SurveyDev {
   int rprec;       // mk_rprec
 
   const float2* R;  // [nw][ns][r_pad] complex FP32 (MK_R_C64)
-  const void* Rq0;  // 16-bit R [nw][ns][2 r_pad] (hi part for split BF16)
-  const void* Rq1;  // lo part of split BF16 R
+  const void* Rq0;  // 16-bit R [nw][ns][2 r_pad] (hi part of split forms)
+  const void* Rq1;  // lo (2-way split) or mid (3-way split) part
+  const void* Rq2;  // lo part of the 3-way split
   void* Bq0;        // 16-bit field embedding [nw][2F][2 r_pad], hi part
-  void* Bq1;        // lo part
+  void* Bq1;        // lo (mid for the 3-way split) part
+  void* Bq2;        // lo part of the 3-way split
   float2* Nw;       // [nw][nw_stride]
   float2* S;        // [nw][s_stride]
   float* fN;        // [F][ns][nt] last N_i
@@ -57,7 +59,9 @@ cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t ro
 cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
                             int num_sms);
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);
-cudaError_t launch_spectrum(const SurveyDev& s, cudaStream_t st, int num_sms);  // band spectrum of the N field
+cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms);  // band spectrum of a field
+cudaError_t launch_inverse(const SurveyDev& s, float* dst, int mode, cudaStream_t st, int num_sms);
+cudaError_t launch_f2p(const SurveyDev& s, float* diff, cudaStream_t st, int num_sms);
 cudaError_t launch_load_rows(const float2* src, float2* dst, int64_t rows, int nrec, int r_pad, cudaStream_t st,
                              int num_sms);
 cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st);

@@ -176,5 +176,21 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
     if ((e = mk::launch_epilogue(v, it & 1, es, stream, num_sms)) != cudaSuccess)
       return set_err(MK_ERR_CUDA, "epilogue launch", cudaGetErrorString(e));
   }
+  // The iterations accumulate f1plus and f1min; N, f2p and pmin follow from
+  // them (the pmin slot of the output serves as the input of its synthesis).
+  if (niter > 0 && (e = mk::launch_inverse(v, v.fN, 0, stream, num_sms)) != cudaSuccess)
+    return set_err(MK_ERR_CUDA, "inverse launch", cudaGetErrorString(e));
+  if ((e = mk::launch_f2p(v, v.pmin, stream, num_sms)) != cudaSuccess)
+    return set_err(MK_ERR_CUDA, "f2p launch", cudaGetErrorString(e));
+  if (niter == 0) {
+    if ((e = cudaMemsetAsync(v.pmin, 0, field * sizeof(float), stream)) != cudaSuccess)
+      return set_err(MK_ERR_CUDA, "cudaMemsetAsync failed", cudaGetErrorString(e));
+  } else {
+    int nl = 0;
+    if ((e = mk::launch_spectrum(v, v.pmin, stream, num_sms)) != cudaSuccess ||
+        (e = mk::launch_contract(v, nullptr, stream, num_sms, &nl)) != cudaSuccess ||
+        (e = mk::launch_inverse(v, v.pmin, 1, stream, num_sms)) != cudaSuccess)
+      return set_err(MK_ERR_CUDA, "pmin synthesis launch", cudaGetErrorString(e));
+  }
   return MK_OK;
 }

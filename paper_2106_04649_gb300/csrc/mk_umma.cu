@@ -9,9 +9,13 @@
 //        B[2f][2r] = Nr, B[2f][2r+1] = -Ni, B[2f+1][2r] = Ni, B[2f+1][2r+1] = Nr,
 //    written directly by the forward-transform epilogue;
 //  * D[k][2f] = Re S, D[k][2f+1] = Im S (FP32 accumulators in TMEM).
-// Precision forms (field split into hi + lo 16-bit parts every iteration):
+// Precision forms (the field is split into 16-bit parts every iteration):
 //  * 16-bit R (BF16 or FP16):  D = R B_hi + R B_lo;
-//  * split BF16 R (hi + lo):   D = R_hi B_hi + R_hi B_lo + R_lo B_hi.
+//  * split BF16 R (hi + lo):   D = R_hi B_hi + R_hi B_lo + R_lo B_hi
+//    (about 16 significant bits per operand);
+//  * 3-way split BF16 (hi + mid + lo for R and the field):
+//    D = hh + hm + mh + hl + lh + mm, the six products down to 2^-16 of the
+//    leading term (about 24 significant bits, FP32-like).
 //
 // Kernel: persistent, one CTA per SM, warp-specialised:
 //  warp 0 lane 0 : TMA producer (3-D tensor maps [K', rows, frequency],
@@ -23,6 +27,11 @@
 //                  signals the epilogue;
 //  warps 2..5    : epilogue, one TMEM lane (= output row) per thread:
 //                  tcgen05.ld -> scale by c -> complex stores to S.
+// Accuracy: the tensor core's FP32 accumulation over a long K chain carries
+// a rounding bias that, on cancelling sums, dominates the operand precision
+// of the split forms.  With PROMOTE the MMAs of each 64-wide K block start a
+// fresh accumulator (two TMEM buffers alternate) and the epilogue warps add
+// each block's partial sums into FP32 registers with round-to-nearest adds.
 // Every mbarrier wait is bounded; on time-out the CTA records an error word,
 // drains its copies and MMAs, frees TMEM and returns.
 
@@ -35,9 +44,10 @@
 namespace mk {
 
 struct UmmaMaps {
-  CUtensorMap a0, a1, b0, b1;
+  CUtensorMap a0, a1, a2, b0, b1, b2;
   int bn;
-  int na;   // 1 or 2 A operands
+  int na;   // 1, 2 or 3 A operands (parts of R)
+  int nb;   // 2 or 3 B operands (parts of the field embedding)
   int fmt;  // 1: bf16, 0: fp16
 };
 
@@ -135,14 +145,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-template <int BN, int NA, int FMT>
+template <int BN, int NA, int NB, int FMT, bool PROMOTE>
 __global__ void __launch_bounds__(kThreads, 1)
 umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                  const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1, UmmaParams P,
+                  const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
+                  const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmB2, UmmaParams P,
                   int stages) {
   constexpr int A_BYTES = UM * UKB * 2;
   constexpr int B_BYTES = BN * UKB * 2;
-  constexpr int STAGE_BYTES = NA * A_BYTES + 2 * B_BYTES;
+  constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
   constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
   constexpr uint32_t IDESC = make_idesc(FMT, BN);
   extern __shared__ uint8_t smem_raw[];
@@ -200,9 +211,11 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, STAGE_BYTES);
           tma_load_3d(base, &tmA0, kb * UKB, mt * UM, m, fb);
-          if (NA == 2) tma_load_3d(base + A_BYTES, &tmA1, kb * UKB, mt * UM, m, fb);
+          if (NA >= 2) tma_load_3d(base + A_BYTES, &tmA1, kb * UKB, mt * UM, m, fb);
+          if (NA >= 3) tma_load_3d(base + 2 * A_BYTES, &tmA2, kb * UKB, mt * UM, m, fb);
           tma_load_3d(base + NA * A_BYTES, &tmB0, kb * UKB, nt * BN, m, fb);
           tma_load_3d(base + NA * A_BYTES + B_BYTES, &tmB1, kb * UKB, nt * BN, m, fb);
+          if (NB >= 3) tma_load_3d(base + NA * A_BYTES + 2 * B_BYTES, &tmB2, kb * UKB, nt * BN, m, fb);
         }
       }
       // no copy may be in flight when the CTA exits
@@ -216,14 +229,25 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
       bool ok = true;
       uint32_t it = 0, tc = 0;
       for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x, ++tc) {
-        const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
-        if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
-          ok = false;
-          break;
+        uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
+        if (!PROMOTE) {
+          if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
         }
-        tc_fence_after();
-        const uint32_t d = tmem_base + acc * BN;
         for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
+          if (PROMOTE) {  // one fresh accumulator per K block, buffers alternate
+            acc = it & 1u;
+            aph = (it >> 1) & 1u;
+            if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t d = tmem_base + acc * BN;
           const int s = (int)(it % (uint32_t)stages);
           const uint32_t ph = (it / (uint32_t)stages) & 1u;
           if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
@@ -232,19 +256,31 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
           }
           tc_fence_after();
           const uint32_t base = ring + (uint32_t)s * STAGE_BYTES;
+          const bool fresh = PROMOTE || kb == 0;
 #pragma unroll
           for (int k4 = 0; k4 < UKB / 16; ++k4) {
             const uint64_t a0 = sw128_desc(base + k4 * 32);
             const uint64_t b0 = sw128_desc(base + NA * A_BYTES + k4 * 32);
             const uint64_t b1 = sw128_desc(base + NA * A_BYTES + B_BYTES + k4 * 32);
-            umma(d, a0, b0, IDESC, (kb > 0 || k4 > 0) ? 1u : 0u);
-            umma(d, a0, b1, IDESC, 1u);
-            if (NA == 2) umma(d, sw128_desc(base + A_BYTES + k4 * 32), b0, IDESC, 1u);
+            umma(d, a0, b0, IDESC, (fresh && k4 == 0) ? 0u : 1u);  // hi * hi
+            umma(d, a0, b1, IDESC, 1u);                             // hi * (lo | mid)
+            if (NA >= 2) {
+              const uint64_t a1 = sw128_desc(base + A_BYTES + k4 * 32);
+              umma(d, a1, b0, IDESC, 1u);                           // (lo | mid) * hi
+              if (NA >= 3) {
+                const uint64_t a2 = sw128_desc(base + 2 * A_BYTES + k4 * 32);
+                const uint64_t b2 = sw128_desc(base + NA * A_BYTES + 2 * B_BYTES + k4 * 32);
+                umma(d, a0, b2, IDESC, 1u);                         // hi * lo
+                umma(d, a2, b0, IDESC, 1u);                         // lo * hi
+                umma(d, a1, b1, IDESC, 1u);                         // mid * mid
+              }
+            }
           }
           umma_commit(smem_u32(&empty_bar[s]));
+          if (PROMOTE) umma_commit(smem_u32(&tfull[acc]));
         }
         if (!ok) break;
-        umma_commit(smem_u32(&tfull[acc]));
+        if (!PROMOTE) umma_commit(smem_u32(&tfull[acc]));
       }
       // every MMA issued by this CTA has completed before TMEM is released
       umma_commit(smem_u32(&drain_bar));
@@ -253,11 +289,47 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
     }
   } else {  // -------------------------------------------------------------- epilogue
     const int quad = warp & 3;  // TMEM lane quadrant this warp may access
-    uint32_t tc = 0;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    uint32_t tc = 0, it = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
       const int m = tile / tiles_per_m;
       const int rem = tile - m * tiles_per_m;
       const int mt = rem / P.ntiles, nt = rem - (rem / P.ntiles) * P.ntiles;
+      const int row = mt * UM + quad * 32 + lane;
+      float2* srow = P.S + (int64_t)m * P.s_stride + (int64_t)row * P.F;
+      if (PROMOTE) {
+        float accv[BN];
+#pragma unroll
+        for (int i = 0; i < BN; ++i) accv[i] = 0.f;
+        bool ok = true;
+        for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
+          const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
+          ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[buf]), ph));
+          if (!ok) break;
+          tc_fence_after();
+#pragma unroll
+          for (int ch = 0; ch < BN / 16; ++ch) {
+            float v[16];
+            tmem_ld16(tmem_base + lane_base + buf * BN + ch * 16, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) accv[ch * 16 + i] += v[i];
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&tempty[buf]));
+        }
+        if (!ok) {
+          if (lane == 0 && P.err) atomicExch(P.err, 13);
+          break;
+        }
+        if (row < P.ns) {
+          const int f0 = nt * BN / 2;
+#pragma unroll
+          for (int j = 0; j < BN / 2; ++j)
+            if (f0 + j < P.F) srow[f0 + j] = make_float2(P.c * accv[2 * j], P.c * accv[2 * j + 1]);
+        }
+        continue;
+      }
       const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[acc]), aph));
       if (!ok) {
@@ -265,12 +337,10 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
         break;
       }
       tc_fence_after();
-      const int row = mt * UM + quad * 32 + lane;
-      float2* srow = P.S + (int64_t)m * P.s_stride + (int64_t)row * P.F;
 #pragma unroll 1
       for (int ch = 0; ch < BN / 16; ++ch) {
         float v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + ch * 16, v);
+        tmem_ld16(tmem_base + lane_base + acc * BN + ch * 16, v);
         if (row < P.ns) {
           const int f0 = (nt * BN + ch * 16) / 2;
 #pragma unroll
@@ -291,21 +361,21 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
   }
 }
 
-template <int BN, int NA, int FMT>
+template <int BN, int NA, int NB>
 int stages_for() {
-  const int stage = NA * UM * UKB * 2 + 2 * BN * UKB * 2;
+  const int stage = NA * UM * UKB * 2 + NB * BN * UKB * 2;
   int st = (kSmemBudget - 1024) / stage;
   return st > kMaxStages ? kMaxStages : st;
 }
 
-template <int BN, int NA, int FMT>
+template <int BN, int NA, int NB, int FMT, bool PROMOTE>
 cudaError_t launch_bn(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, int num_sms) {
-  const int stages = stages_for<BN, NA, FMT>();
-  const int stage = NA * UM * UKB * 2 + 2 * BN * UKB * 2;
+  const int stages = stages_for<BN, NA, NB>();
+  const int stage = NA * UM * UKB * 2 + NB * BN * UKB * 2;
   const size_t smem = (size_t)stages * stage + 1024;
   static bool attr_done = false;  // set once per process (same value for every device)
   if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(umma_cgemm_kernel<BN, NA, FMT>,
+    cudaError_t e = cudaFuncSetAttribute(umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
@@ -323,17 +393,18 @@ cudaError_t launch_bn(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, i
   P.err = s.err;
   const int64_t tiles = (int64_t)P.nw * P.mtiles * P.ntiles;
   const int grid = (int)(tiles < num_sms ? tiles : num_sms);
-  umma_cgemm_kernel<BN, NA, FMT><<<grid, kThreads, smem, st>>>(mp.a0, mp.a1, mp.b0, mp.b1, P, stages);
+  umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE><<<grid, kThreads, smem, st>>>(mp.a0, mp.a1, mp.a2, mp.b0, mp.b1, mp.b2, P,
+                                                                    stages);
   return cudaGetLastError();
 }
 
-template <int NA, int FMT>
+template <int NA, int NB, int FMT, bool PROMOTE>
 cudaError_t launch_na(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, int num_sms) {
   switch (mp.bn) {
-    case 16: return launch_bn<16, NA, FMT>(s, mp, st, num_sms);
-    case 32: return launch_bn<32, NA, FMT>(s, mp, st, num_sms);
-    case 64: return launch_bn<64, NA, FMT>(s, mp, st, num_sms);
-    default: return launch_bn<128, NA, FMT>(s, mp, st, num_sms);
+    case 16: return launch_bn<16, NA, NB, FMT, PROMOTE>(s, mp, st, num_sms);
+    case 32: return launch_bn<32, NA, NB, FMT, PROMOTE>(s, mp, st, num_sms);
+    case 64: return launch_bn<64, NA, NB, FMT, PROMOTE>(s, mp, st, num_sms);
+    default: return launch_bn<128, NA, NB, FMT, PROMOTE>(s, mp, st, num_sms);
   }
 }
 
@@ -378,13 +449,16 @@ int umma_bn(int F) {
 UmmaMaps* umma_create(const SurveyDev& s) {
   UmmaMaps* mp = new UmmaMaps();
   mp->bn = umma_bn(s.F);
-  mp->na = s.rprec == 3 ? 2 : 1;
+  mp->na = s.rprec == 3 ? 2 : (s.rprec == 4 ? 3 : 1);
+  mp->nb = s.rprec == 4 ? 3 : 2;
   mp->fmt = s.rprec == 2 ? 0 : 1;
   const int kp = 2 * s.r_pad;
   bool ok = encode_map(&mp->a0, s.Rq0, kp, s.ns, s.nw, UM, mp->fmt) &&
-            encode_map(&mp->a1, mp->na == 2 ? s.Rq1 : s.Rq0, kp, s.ns, s.nw, UM, mp->fmt) &&
+            encode_map(&mp->a1, mp->na >= 2 ? s.Rq1 : s.Rq0, kp, s.ns, s.nw, UM, mp->fmt) &&
+            encode_map(&mp->a2, mp->na >= 3 ? s.Rq2 : s.Rq0, kp, s.ns, s.nw, UM, mp->fmt) &&
             encode_map(&mp->b0, s.Bq0, kp, 2 * s.F, s.nw, mp->bn, mp->fmt) &&
-            encode_map(&mp->b1, s.Bq1, kp, 2 * s.F, s.nw, mp->bn, mp->fmt);
+            encode_map(&mp->b1, s.Bq1, kp, 2 * s.F, s.nw, mp->bn, mp->fmt) &&
+            encode_map(&mp->b2, mp->nb >= 3 ? s.Bq2 : s.Bq1, kp, 2 * s.F, s.nw, mp->bn, mp->fmt);
   if (!ok) {
     delete mp;
     return nullptr;
@@ -396,9 +470,11 @@ void umma_destroy(UmmaMaps* mp) { delete mp; }
 
 cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms) {
   if (!mp) return cudaErrorInvalidValue;
-  if (mp->na == 2) return launch_na<2, 1>(s, *mp, st, num_sms);
-  if (mp->fmt == 1) return launch_na<1, 1>(s, *mp, st, num_sms);
-  return launch_na<1, 0>(s, *mp, st, num_sms);
+  // the split forms target FP32-level accuracy: they promote per K block
+  if (mp->na == 3) return launch_na<3, 3, 1, true>(s, *mp, st, num_sms);
+  if (mp->na == 2) return launch_na<2, 2, 1, true>(s, *mp, st, num_sms);
+  if (mp->fmt == 1) return launch_na<1, 2, 1, false>(s, *mp, st, num_sms);
+  return launch_na<1, 2, 0, false>(s, *mp, st, num_sms);
 }
 
 }  // namespace mk

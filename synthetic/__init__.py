@@ -28,6 +28,7 @@ from .layered import (  # noqa: F401
     splitmix64_mix,
     SplitMix64,
     first_arrival_times,
+    focal_shard,
     survey_td,
 )
 from .configs import (  # noqa: F401

@@ -315,6 +315,12 @@ def focal_line(s_n: int, dx: float, count: int, z: float, mode: str = "central80
     return np.stack([xs, np.full_like(xs, z)], axis=1)
 
 
+def focal_shard(focal: np.ndarray, world: int, rank: int) -> np.ndarray:
+    """Focal points of one rank when a focal line is split over ``world``
+    ranks: rank r takes points r, r + world, r + 2 world, ..."""
+    return np.asarray(focal)[rank::world]
+
+
 def survey_td(s: Survey) -> np.ndarray:
     """t_d[F][n] for every focal point of the survey."""
     return np.stack([first_arrival_times(s.model, xf, zf, s.x) for xf, zf in s.focal])
