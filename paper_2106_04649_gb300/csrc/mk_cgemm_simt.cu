@@ -1,6 +1,6 @@
 // The contraction of Eq. (1) for many focal points with complex FP32 R: a
 // register-tiled SIMT complex GEMM per frequency,
-// S_m[k][f] = c * sum_r R_m[k][r] Nw_m[r][f], with exact FP32 products
+// S_m[k][f] = c * sum_r R_m[k][r] Nw_m[f][r], with exact FP32 products
 // (the plain-precision form; the tensor-core forms are in mk_umma.cu).
 // 64 x 64 output tile per CTA, 16-deep K slices double-buffered through
 // shared memory with register prefetch, 4 x 4 complex accumulators per
@@ -14,53 +14,45 @@ namespace {
 
 constexpr int GM = 64, GN = 64, GK = 16;
 
-// C_m[k][f] = c * sum_r A_m[k][r] B_m[r][f]; A = R_m (rows of r_pad, zero
-// padded, so K needs no predicate), B = Nw_m ([r][f], row stride F),
-// C = S_m ([k][f], row stride F).  blockIdx = (k tile, f tile, m).
+// C_m[k][f] = c * sum_r A_m[k][r] B_m[f][r]; A = R_m (rows of r_pad, zero
+// padded, so K needs no predicate), B = Nw_m ([f][r_pad], K-contiguous),
+// C = S_m[f * ns + k].  blockIdx = (k tile, f tile, m).  Thread (tx, ty)
+// owns rows k = k0 + tx + 16 i and columns f = f0 + 4 ty + j, so that a
+// half-warp stores 16 consecutive k of one f (coalesced).
 __global__ void __launch_bounds__(256)
 cgemm_f32_kernel(const float2* __restrict__ R, const float2* __restrict__ Nw, float2* __restrict__ S, int ns, int F,
                  int r_pad, int64_t nw_stride, int64_t s_stride, float c) {
-  __shared__ __align__(16) float2 As[2][GK][GM];  // transposed A tile: As[r][k]
-  __shared__ __align__(16) float2 Bs[2][GK][GN];
+  __shared__ __align__(16) float2 As[2][GK][GM];  // As[r][k]
+  __shared__ __align__(16) float2 Bs[2][GK][GN];  // Bs[r][f]
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
   const int m = blockIdx.z;
   const int k0 = blockIdx.x * GM, f0 = blockIdx.y * GN;
   const float2* A = R + (int64_t)m * ns * r_pad;
   const float2* B = Nw + (int64_t)m * nw_stride;
-  // global -> register staging: A: row ak = t/4, complex cols (t%4)*2 + {0,1} and +8
-  const int ak = t >> 2, ac = (t & 3) * 2;
-  const bool arow_ok = k0 + ak < ns;
-  const float2* Ap = A + (int64_t)(k0 + ak) * r_pad + ac;
-  // B: rows br = t/32 and br + 8, complex cols (t%32)*2 + {0,1}
-  const int br = t >> 5, bc = (t & 31) * 2;
-  const bool bc0 = f0 + bc < F, bc1 = f0 + bc + 1 < F;
-  float4 ra0, ra1;
-  float2 rb[2][2];
+  // global -> register staging: row (t / 4) of the tile, complex cols (t % 4) * 2 + {0, 1} and + 8
+  const int lr = t >> 2, lc = (t & 3) * 2;
+  const bool arow_ok = k0 + lr < ns;
+  const bool brow_ok = f0 + lr < F;
+  const float2* Ap = A + (int64_t)(k0 + lr) * r_pad + lc;
+  const float2* Bp = B + (int64_t)(f0 + lr) * r_pad + lc;
+  float4 ra0, ra1, rb0, rb1;
   auto load_tile = [&](int kb) {
-    if (arow_ok) {
-      ra0 = __ldg(reinterpret_cast<const float4*>(Ap + kb));
-      ra1 = __ldg(reinterpret_cast<const float4*>(Ap + kb + 8));
-    } else {
-      ra0 = ra1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float2* bp = B + (int64_t)(kb + br + 8 * h) * F + f0 + bc;
-      rb[h][0] = bc0 ? __ldg(bp) : make_float2(0.f, 0.f);
-      rb[h][1] = bc1 ? __ldg(bp + 1) : make_float2(0.f, 0.f);
-    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    ra0 = arow_ok ? __ldg(reinterpret_cast<const float4*>(Ap + kb)) : z;
+    ra1 = arow_ok ? __ldg(reinterpret_cast<const float4*>(Ap + kb + 8)) : z;
+    rb0 = brow_ok ? __ldg(reinterpret_cast<const float4*>(Bp + kb)) : z;
+    rb1 = brow_ok ? __ldg(reinterpret_cast<const float4*>(Bp + kb + 8)) : z;
   };
   auto store_tile = [&](int buf) {
-    As[buf][ac][ak] = make_float2(ra0.x, ra0.y);
-    As[buf][ac + 1][ak] = make_float2(ra0.z, ra0.w);
-    As[buf][ac + 8][ak] = make_float2(ra1.x, ra1.y);
-    As[buf][ac + 9][ak] = make_float2(ra1.z, ra1.w);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      Bs[buf][br + 8 * h][bc] = rb[h][0];
-      Bs[buf][br + 8 * h][bc + 1] = rb[h][1];
-    }
+    As[buf][lc][lr] = make_float2(ra0.x, ra0.y);
+    As[buf][lc + 1][lr] = make_float2(ra0.z, ra0.w);
+    As[buf][lc + 8][lr] = make_float2(ra1.x, ra1.y);
+    As[buf][lc + 9][lr] = make_float2(ra1.z, ra1.w);
+    Bs[buf][lc][lr] = make_float2(rb0.x, rb0.y);
+    Bs[buf][lc + 1][lr] = make_float2(rb0.z, rb0.w);
+    Bs[buf][lc + 8][lr] = make_float2(rb1.x, rb1.y);
+    Bs[buf][lc + 9][lr] = make_float2(rb1.z, rb1.w);
   };
   float accr[4][4], acci[4][4];
 #pragma unroll
@@ -77,13 +69,13 @@ cgemm_f32_kernel(const float2* __restrict__ R, const float2* __restrict__ Nw, fl
     if (kt + 1 < nk) load_tile((kt + 1) * GK);
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      const float4 a01 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-      const float4 a23 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4 + 2]);
-      const float2 a[4] = {make_float2(a01.x, a01.y), make_float2(a01.z, a01.w), make_float2(a23.x, a23.y),
-                           make_float2(a23.z, a23.w)};
-      float2 b[4];
+      float2 a[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+      for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tx + 16 * i];
+      const float4 b01 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
+      const float4 b23 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4 + 2]);
+      const float2 b[4] = {make_float2(b01.x, b01.y), make_float2(b01.z, b01.w), make_float2(b23.x, b23.y),
+                           make_float2(b23.z, b23.w)};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -97,15 +89,15 @@ cgemm_f32_kernel(const float2* __restrict__ R, const float2* __restrict__ Nw, fl
     if (kt + 1 < nk) store_tile(buf ^ 1);
     __syncthreads();
   }
+  float2* Sm = S + (int64_t)m * s_stride;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int k = k0 + ty * 4 + i;
-    if (k >= ns) continue;
-    float2* crow = S + (int64_t)m * s_stride + (int64_t)k * F;
+  for (int j = 0; j < 4; ++j) {
+    const int f = f0 + ty * 4 + j;
+    if (f >= F) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int f = f0 + tx + 16 * j;
-      if (f < F) crow[f] = make_float2(c * accr[i][j], c * acci[i][j]);
+    for (int i = 0; i < 4; ++i) {
+      const int k = k0 + tx + 16 * i;
+      if (k < ns) Sm[(int64_t)f * ns + k] = make_float2(c * accr[i][j], c * acci[i][j]);
     }
   }
 }

@@ -164,10 +164,7 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
   __syncthreads();
 }
 
-__device__ __forceinline__ int64_t field_offset(const SurveyDev& s, int t) {
-  const int f = t % s.F, k = t / s.F;
-  return ((int64_t)f * s.ns + k) * s.nt;
-}
+__device__ __forceinline__ int64_t field_offset(const SurveyDev& s, int t) { return (int64_t)t * s.nt; }
 
 // Two 16-bit values packed in 32 bits (low half first in memory).
 template <bool BF16>
@@ -190,7 +187,7 @@ __device__ __forceinline__ float round16(float a) {
 // rows 2f: (Nr, -Ni), 2f+1: (Ni, Nr) at columns 2k, 2k+1.
 template <bool BF16>
 __device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int t, float nr, float ni) {
-  const int f = t % s.F, k = t / s.F;
+  const int f = t / s.ns, k = t - (t / s.ns) * s.ns;
   const int64_t kp = 2 * (int64_t)s.r_pad;
   const int64_t e0 = ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k;
   uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
@@ -228,7 +225,13 @@ __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x,
     const float dx = zm.x - zc.x, dy = zm.y - zc.y;
     const float2 B = hasb ? make_float2(0.5f * dy, -0.5f * dx) : make_float2(0.f, 0.f);
     if (s.rprec == 0) {
-      *reinterpret_cast<float4*>(s.Nw + (int64_t)m * s.nw_stride + t0) = make_float4(A.x, A.y, B.x, B.y);
+      const int fa = t0 / s.ns, ka = t0 - fa * s.ns;
+      float2* row = s.Nw + (int64_t)m * s.nw_stride;
+      row[(int64_t)fa * s.r_pad + ka] = A;
+      if (hasb) {
+        const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
+        row[(int64_t)fb * s.r_pad + kb] = B;
+      }
     } else if (s.rprec == 2) {
       store_embedding<false>(s, m, t0, A.x, A.y);
       if (hasb) store_embedding<false>(s, m, t0 + 1, B.x, B.y);
@@ -349,7 +352,7 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
     __threadfence();
     for (int f = threadIdx.x; f < s.F; f += THREADS) {
       double acc = 0.0;
-      for (int k = 0; k < s.ns; ++k) acc += __ldcg(s.Epart + (int64_t)k * s.F + f);
+      for (int k = 0; k < s.ns; ++k) acc += __ldcg(s.Epart + (int64_t)f * s.ns + k);
       energy_slot[f] = acc;
     }
     if (threadIdx.x == 0) *s.counter = 0u;
@@ -401,8 +404,7 @@ init_kernel(SurveyDev s, const float* __restrict__ Gd) {
 __global__ void window_kernel(SurveyDev s, const double* __restrict__ td, double eps) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= s.ncols) return;
-  const int f = t % s.F, k = t / s.F;
-  const double T = td[(int64_t)f * s.ns + k] - eps;
+  const double T = td[t] - eps;  // t = f * ns + k, the layout of t_d [F][ns]
   int L = 0;
   if (T > 0.0 && isfinite(T)) {
     const double q = ceil(T / s.dt);

@@ -7,10 +7,12 @@
 namespace mk {
 
 // Device-side view of one survey: sizes, strides and workspace carvings.
-// Trace ("column") index t = k * F + f; field offset of trace (k, f) is
-// (f * ns + k) * nt.  S and Nw are frequency-major: element (m, t) lives at
-// m * s_stride + t (S) and m * nw_stride + t (Nw).  For F = 1, Nw rows are
-// r_pad long and the entries t >= ns stay zero.
+// Traces are ordered focal-major: t = f * ns + k, so that neighbouring
+// traces (same focal point, neighbouring positions) touch neighbouring
+// addresses in every spectrum buffer.  Field offset of trace t is t * nt.
+// S is frequency-major with element (m, t) at m * s_stride + t.  Nw holds
+// [nw][F][r_pad]: element (m, f, r) at m * nw_stride + f * r_pad + r, the
+// padding r >= ns zero.
 struct SurveyDev {
   int ns;          // positions (nsrc == nrec)
   int nt;          // samples
@@ -19,7 +21,7 @@ struct SurveyDev {
   int r_pad;       // padded row length of R (multiple of 32)
   int ncols;       // ns * F
   int64_t s_stride;   // complex elements per S row (>= ncols + 1, multiple of 4)
-  int64_t nw_stride;  // complex elements per Nw row (r_pad * F)
+  int64_t nw_stride;  // complex elements per Nw frequency (F * r_pad)
   double dt;       // sample interval (s)
   float c;         // synthesis scale dx * dt
   float inv_nt;    // 1 / nt
@@ -32,7 +34,7 @@ struct SurveyDev {
   void* Bq0;        // 16-bit field embedding [nw][2F][2 r_pad], hi part
   void* Bq1;        // lo (mid for the 3-way split) part
   void* Bq2;        // lo part of the 3-way split
-  float2* Nw;       // [nw][nw_stride]
+  float2* Nw;       // [nw][F][r_pad]
   float2* S;        // [nw][s_stride]
   float* fN;        // [F][ns][nt] last N_i
   float* f1p;

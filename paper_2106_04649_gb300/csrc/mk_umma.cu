@@ -296,7 +296,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
       const int rem = tile - m * tiles_per_m;
       const int mt = rem / P.ntiles, nt = rem - (rem / P.ntiles) * P.ntiles;
       const int row = mt * UM + quad * 32 + lane;
-      float2* srow = P.S + (int64_t)m * P.s_stride + (int64_t)row * P.F;
+      float2* scol = P.S + (int64_t)m * P.s_stride + row;  // S[m][f * ns + row]: lanes write consecutive rows
       if (PROMOTE) {
         float accv[BN];
 #pragma unroll
@@ -326,7 +326,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
           const int f0 = nt * BN / 2;
 #pragma unroll
           for (int j = 0; j < BN / 2; ++j)
-            if (f0 + j < P.F) srow[f0 + j] = make_float2(P.c * accv[2 * j], P.c * accv[2 * j + 1]);
+            if (f0 + j < P.F) scol[(int64_t)(f0 + j) * P.ns] = make_float2(P.c * accv[2 * j], P.c * accv[2 * j + 1]);
         }
         continue;
       }
@@ -345,7 +345,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
           const int f0 = (nt * BN + ch * 16) / 2;
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            if (f0 + j < P.F) srow[f0 + j] = make_float2(P.c * v[2 * j], P.c * v[2 * j + 1]);
+            if (f0 + j < P.F) scol[(int64_t)(f0 + j) * P.ns] = make_float2(P.c * v[2 * j], P.c * v[2 * j + 1]);
         }
       }
       tc_fence_before();
