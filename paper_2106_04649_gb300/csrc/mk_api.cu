@@ -157,6 +157,29 @@ size_t layout(Survey& sv, char* base) {
   return off;
 }
 
+// Twiddles of the shared-memory FFT (mk_fft.cu), pass by pass: radix-8
+// passes, then one radix-2 or radix-4 pass when log2 nt is not a multiple of
+// 3; pass (R, Ns) stores e^{-2 pi i r k / (Ns R)} at [(r - 1) Ns + k],
+// r = 1 .. R-1, k < Ns, tables back to back (nt - 1 entries).  FP64, rounded.
+void fill_twiddles(std::vector<float2>& tw, int nt) {
+  int lg = 0;
+  while ((1 << lg) < nt) ++lg;
+  int Ns = 1, toff = 0;
+  auto pass = [&](int R) {
+    for (int r = 1; r < R; ++r)
+      for (int k = 0; k < Ns; ++k) {
+        const long long q = (long long)r * k * (nt / (Ns * R));  // exponent in units of 1/nt
+        const double a = -2.0 * M_PI * (double)q / (double)nt;
+        tw[toff + (r - 1) * Ns + k] = make_float2((float)cos(a), (float)sin(a));
+      }
+    toff += (R - 1) * Ns;
+    Ns *= R;
+  };
+  for (int p = 0; p < lg / 3; ++p) pass(8);
+  if (lg % 3 == 1) pass(2);
+  if (lg % 3 == 2) pass(4);
+}
+
 mk_status get_survey(mk_plan_t p, int32_t survey, Survey** out) {
   if (!p) return fail(nullptr, MK_ERR_ARG, "null plan");
   if (survey < 0 || survey >= (int32_t)p->s.size())
@@ -325,11 +348,8 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
       }
     }
     const int nt = sv.dev.nt;
-    std::vector<float2> tw(nt);
-    for (int q = 0; q < nt; ++q) {
-      const double a = -2.0 * M_PI * (double)q / (double)nt;
-      tw[q] = make_float2((float)cos(a), (float)sin(a));
-    }
+    std::vector<float2> tw(nt, make_float2(0.f, 0.f));
+    fill_twiddles(tw, nt);
     e = cudaMemcpyAsync(const_cast<float2*>(sv.dev.tw), tw.data(), nt * sizeof(float2), cudaMemcpyHostToDevice,
                         p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);

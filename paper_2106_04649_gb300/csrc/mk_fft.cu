@@ -22,10 +22,12 @@
 // Two real traces share one complex transform (a + i b): the inverse
 // transform of X + iY with Hermitian X, Y gives x + iy; the forward transform
 // Z of a + ib gives A_m = (Z_m + conj Z_{-m})/2, B_m = (Z_m - conj Z_{-m})/(2i).
-// The complex transform is a Stockham autosort FFT (radix 4, one radix-2
-// stage when log2 nt is odd) in shared memory with twiddles from an FP64 host
-// table rounded to FP32.  One CTA processes one pair of traces at a time and
-// loops over pairs (grid sized to the SM count).
+// The complex transform is a Stockham autosort FFT in shared memory with
+// twiddles from an FP64 host
+// table rounded to FP32 (radix-8 passes, contiguous per-pass twiddle tables
+// and a padded shared-memory index keep the accesses bank-conflict free).
+// One CTA processes one pair of traces at a time and loops over pairs
+// (grid sized to the SM count).
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -60,82 +62,105 @@ __device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2&
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n / 2); }
 __host__ __device__ constexpr int threads_for(int nt) { return nt / 8 < 32 ? 32 : (nt / 8 > 512 ? 512 : nt / 8); }
 
-// In-place complex DFT of x[0..NT) (unnormalised; sign -1 forward, +1 inverse).
-// Stockham stage with current sub-length Ns and radix R: butterfly j
-// (k = j mod Ns) reads x[j + r NT/R], applies twiddles w^{r k NT/(Ns R)},
-// does a length-R DFT and writes x[(j - k) R + k + r Ns].  Reads and writes
-// of a stage are separated by a barrier, so the stage works in place.
+// Shared-memory index with one float2 of padding after every 16: the strided
+// writes of the early passes then hit distinct banks per half-warp.
+__device__ __forceinline__ int P(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded(int n) { return n + n / 16; }
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  // radix-2 split into even/odd outputs: a_n = v_n + v_{n+4} -> DFT4 gives
+  // V_{2m}; b_n = (v_n - v_{n+4}) W8^{+-n} -> DFT4 gives V_{2m+1}
+  const float c = 0.70710678118654752f;
+  float2 a0 = cadd(v[0], v[4]), a1 = cadd(v[1], v[5]), a2 = cadd(v[2], v[6]), a3 = cadd(v[3], v[7]);
+  float2 b0 = csub(v[0], v[4]), b1 = csub(v[1], v[5]), b2 = csub(v[2], v[6]), b3 = csub(v[3], v[7]);
+  b1 = INV ? make_float2(c * (b1.x - b1.y), c * (b1.x + b1.y)) : make_float2(c * (b1.x + b1.y), c * (b1.y - b1.x));
+  b2 = mul_mi<INV>(b2);
+  b3 = INV ? make_float2(-c * (b3.x + b3.y), c * (b3.x - b3.y)) : make_float2(c * (b3.y - b3.x), -c * (b3.x + b3.y));
+  dft4<INV>(a0, a1, a2, a3);
+  dft4<INV>(b0, b1, b2, b3);
+  v[0] = a0;
+  v[2] = a1;
+  v[4] = a2;
+  v[6] = a3;
+  v[1] = b0;
+  v[3] = b1;
+  v[5] = b2;
+  v[7] = b3;
+}
+
+template <bool INV, int R>
+__device__ __forceinline__ void dftR(float2 (&v)[R]) {
+  if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else {
+    const float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+}
+
+// One Stockham pass of radix R with current sub-length Ns: butterfly j
+// (k = j mod Ns) reads x[j + r NT/R], multiplies by w^{r k NT/(Ns R)} =
+// e^{-+2 pi i r k / (Ns R)}, does a length-R DFT and writes
+// x[(j - k) R + k + r Ns].  The pass's twiddles are a contiguous table
+// tw[toff + (r - 1) Ns + k] (consecutive k on consecutive lanes).  Reads and
+// writes are separated by a barrier, so the pass works in place.
+template <int NT, int THREADS, bool INV, int R>
+__device__ __forceinline__ void stockham_pass(float2* x, const float2* tw, int Ns, int toff) {
+  constexpr int NB = NT / R;
+  constexpr int PB = (NB + THREADS - 1) / THREADS;
+  float2 v[PB][R];
+#pragma unroll
+  for (int q = 0; q < PB; ++q) {
+    const int j = threadIdx.x + q * THREADS;
+    if (j < NB) {
+      const int k = j & (Ns - 1);
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][r] = x[P(j + r * NB)];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[toff + (r - 1) * Ns + k];
+        if (INV) w.y = -w.y;
+        v[q][r] = cmul(v[q][r], w);
+      }
+      dftR<INV, R>(v[q]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PB; ++q) {
+    const int j = threadIdx.x + q * THREADS;
+    if (j < NB) {
+      const int k = j & (Ns - 1);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[P(base + r * Ns)] = v[q][r];
+    }
+  }
+  __syncthreads();
+}
+
+// In-place complex DFT of x[P(0 .. NT-1)] (unnormalised; sign -1 forward,
+// +1 inverse): radix-8 passes, then one radix-2 or radix-4 pass when log2 NT
+// is not a multiple of 3.  The twiddle table holds the passes' tables back to
+// back (NT - 1 entries in all, see fill_twiddles on the host).
 template <int NT, int THREADS, bool INV>
 __device__ __forceinline__ void fft_smem(float2* x, const float2* tw) {
   constexpr int LOG2 = ilog2(NT);
-  constexpr int NB4 = NT / 4;
-  constexpr int P4 = (NB4 + THREADS - 1) / THREADS;
-  int Ns = 1;
+  constexpr int N8 = LOG2 / 3;
+  constexpr int REM = LOG2 % 3;
+  int Ns = 1, toff = 0;
 #pragma unroll 1
-  for (int s = 0; s < LOG2 / 2; ++s) {
-    float2 v[P4][4];
-    const int step = NT / (Ns * 4);
-#pragma unroll
-    for (int q = 0; q < P4; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      if (j < NB4) {
-        const int k = j & (Ns - 1);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) v[q][r] = x[j + r * NB4];
-#pragma unroll
-        for (int r = 1; r < 4; ++r) {
-          float2 w = tw[r * k * step];
-          if (INV) w.y = -w.y;
-          v[q][r] = cmul(v[q][r], w);
-        }
-        dft4<INV>(v[q][0], v[q][1], v[q][2], v[q][3]);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < P4; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      if (j < NB4) {
-        const int k = j & (Ns - 1);
-        const int base = (j - k) * 4 + k;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) x[base + r * Ns] = v[q][r];
-      }
-    }
-    __syncthreads();
-    Ns *= 4;
+  for (int p = 0; p < N8; ++p) {
+    stockham_pass<NT, THREADS, INV, 8>(x, tw, Ns, toff);
+    toff += 7 * Ns;
+    Ns *= 8;
   }
-  if (LOG2 & 1) {
-    constexpr int NB2 = NT / 2;
-    constexpr int P2 = (NB2 + THREADS - 1) / THREADS;
-    float2 v[P2][2];
-#pragma unroll
-    for (int q = 0; q < P2; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      if (j < NB2) {
-        const int k = j & (Ns - 1);
-        v[q][0] = x[j];
-        float2 w = tw[k * (NT / (Ns * 2))];
-        if (INV) w.y = -w.y;
-        v[q][1] = cmul(x[j + NB2], w);
-        const float2 a = v[q][0];
-        v[q][0] = cadd(a, v[q][1]);
-        v[q][1] = csub(a, v[q][1]);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < P2; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      if (j < NB2) {
-        const int k = j & (Ns - 1);
-        const int base = (j - k) * 2 + k;
-        x[base] = v[q][0];
-        x[base + Ns] = v[q][1];
-      }
-    }
-    __syncthreads();
-  }
+  if (REM == 1) stockham_pass<NT, THREADS, INV, 2>(x, tw, Ns, toff);
+  if (REM == 2) stockham_pass<NT, THREADS, INV, 4>(x, tw, Ns, toff);
 }
 
 // Block-wide sum of two doubles in a fixed order (deterministic).
@@ -219,8 +244,8 @@ __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x,
                                                   int t0, bool hasb) {
   fft_smem<NT, THREADS, false>(x, tw);
   for (int m = threadIdx.x; m < s.nw; m += THREADS) {
-    const float2 zm = x[m];
-    const float2 zc = cconj(x[(NT - m) & (NT - 1)]);
+    const float2 zm = x[P(m)];
+    const float2 zc = cconj(x[P((NT - m) & (NT - 1))]);
     const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
     const float dx = zm.x - zc.x, dy = zm.y - zc.y;
     const float2 B = hasb ? make_float2(0.5f * dy, -0.5f * dx) : make_float2(0.f, 0.f);
@@ -266,8 +291,8 @@ __device__ __forceinline__ void pack_pair(const SurveyDev& s, float2* x, int t0,
       X.y = 0.f;
       Y.y = 0.f;
     }
-    x[m] = make_float2(X.x - Y.y, X.y + Y.x);
-    if (m > 0 && m < NT / 2) x[NT - m] = make_float2(X.x + Y.y, Y.x - X.y);
+    x[P(m)] = make_float2(X.x - Y.y, X.y + Y.x);
+    if (m > 0 && m < NT / 2) x[P(NT - m)] = make_float2(X.x + Y.y, Y.x - X.y);
   }
 }
 
@@ -278,8 +303,8 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
   constexpr int PJ = NT / THREADS;  // samples per thread
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);  // inverse transform
-  float2* y = x + NT;                               // N_i pair for the forward transform
-  float2* tw = y + NT;
+  float2* y = x + padded(NT);                       // N_i pair for the forward transform
+  float2* tw = y + padded(NT);
   __shared__ double red[2 * (THREADS / 32)];
   __shared__ int s_last;
 
@@ -315,12 +340,12 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
     for (int q = 0; q < PJ; ++q) {
       const int j = threadIdx.x + q * THREADS;
       const int d = j < NT - j ? j : NT - j;  // |signed index|
-      const float2 zj = x[j];
-      const float2 zr = x[(NT - j) & (NT - 1)];
+      const float2 zj = x[P(j)];
+      const float2 zr = x[P((NT - j) & (NT - 1))];
       const float sa = zj.x * inv, sb = zj.y * inv;
       const float na = d < La ? -(zr.x * inv) : 0.f;
       const float nb = d < Lb ? -(zr.y * inv) : 0.f;
-      y[j] = make_float2(na, nb);
+      y[P(j)] = make_float2(na, nb);
       if (d < La) {
         f1[ba + j] = ha[q] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
         ea += (double)na * (double)na;
@@ -366,7 +391,7 @@ init_kernel(SurveyDev s, const float* __restrict__ Gd) {
   constexpr int PJ = NT / THREADS;
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = x + NT;
+  float2* tw = x + padded(NT);
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
   __syncthreads();
   const int npairs = (s.ncols + 1) / 2;
@@ -381,7 +406,7 @@ init_kernel(SurveyDev s, const float* __restrict__ Gd) {
       const int jr = (NT - j) & (NT - 1);
       const float na = Gd[ba + jr];  // G_d has the field layout [F][nrec][nt]
       const float nb = hasb ? Gd[bb + jr] : 0.f;
-      x[j] = make_float2(na, nb);
+      x[P(j)] = make_float2(na, nb);
       s.fN[ba + j] = na;
       s.f1p[ba + j] = na;
       s.f1m[ba + j] = 0.f;
@@ -424,7 +449,7 @@ spectrum_kernel(SurveyDev s, const float* __restrict__ src) {
   constexpr int THREADS = threads_for(NT);
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = x + NT;
+  float2* tw = x + padded(NT);
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
   __syncthreads();
   const int npairs = (s.ncols + 1) / 2;
@@ -434,7 +459,7 @@ spectrum_kernel(SurveyDev s, const float* __restrict__ src) {
     const int64_t ba = field_offset(s, t0);
     const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
     for (int j = threadIdx.x; j < NT; j += THREADS)
-      x[j] = make_float2(src[ba + j], hasb ? src[bb + j] : 0.f);
+      x[P(j)] = make_float2(src[ba + j], hasb ? src[bb + j] : 0.f);
     __syncthreads();
     forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
     __syncthreads();
@@ -450,7 +475,7 @@ inverse_kernel(SurveyDev s, float* __restrict__ dst, int mode) {
   constexpr int THREADS = threads_for(NT);
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = x + NT;
+  float2* tw = x + padded(NT);
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
   __syncthreads();
   const int npairs = (s.ncols + 1) / 2;
@@ -468,11 +493,11 @@ inverse_kernel(SurveyDev s, float* __restrict__ dst, int mode) {
       float va, vb;
       if (mode == 0) {
         const int d = j < NT - j ? j : NT - j;
-        const float2 zr = x[(NT - j) & (NT - 1)];
+        const float2 zr = x[P((NT - j) & (NT - 1))];
         va = d < La ? -(zr.x * s.inv_nt) : 0.f;
         vb = d < Lb ? -(zr.y * s.inv_nt) : 0.f;
       } else {
-        const float2 z = x[j];
+        const float2 z = x[P(j)];
         va = z.x * s.inv_nt;
         vb = z.y * s.inv_nt;
       }
@@ -510,16 +535,15 @@ __global__ void green_kernel(SurveyDev s, float* __restrict__ out) {
 
 template <int NT>
 cudaError_t set_attrs() {
-  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       3 * NT * (int)sizeof(float2));
+  constexpr int one = (padded(NT) + NT) * (int)sizeof(float2);
+  constexpr int two = (2 * padded(NT) + NT) * (int)sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, two);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * NT * (int)sizeof(float2));
+  e = cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(spectrum_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           2 * NT * (int)sizeof(float2));
+  e = cudaFuncSetAttribute(spectrum_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(inverse_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              2 * NT * (int)sizeof(float2));
+  return cudaFuncSetAttribute(inverse_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
 }
 
 template <int NT>
@@ -527,7 +551,7 @@ cudaError_t launch_inv_nt(const SurveyDev& s, float* dst, int mode, cudaStream_t
   const int npairs = (s.ncols + 1) / 2;
   int grid = num_sms * 4;
   if (grid > npairs) grid = npairs;
-  inverse_kernel<NT><<<grid, threads_for(NT), 2 * NT * sizeof(float2), st>>>(s, dst, mode);
+  inverse_kernel<NT><<<grid, threads_for(NT), (padded(NT) + NT) * sizeof(float2), st>>>(s, dst, mode);
   return cudaGetLastError();
 }
 
@@ -536,7 +560,7 @@ cudaError_t launch_spec_nt(const SurveyDev& s, const float* src, cudaStream_t st
   const int npairs = (s.ncols + 1) / 2;
   int grid = num_sms * 4;
   if (grid > npairs) grid = npairs;
-  spectrum_kernel<NT><<<grid, threads_for(NT), 2 * NT * sizeof(float2), st>>>(s, src);
+  spectrum_kernel<NT><<<grid, threads_for(NT), (padded(NT) + NT) * sizeof(float2), st>>>(s, src);
   return cudaGetLastError();
 }
 
@@ -546,7 +570,7 @@ cudaError_t launch_epi_nt(const SurveyDev& s, int odd, double* slot, cudaStream_
   const int per_sm = NT >= 4096 ? 2 : 4;
   int grid = num_sms * per_sm;
   if (grid > npairs) grid = npairs;
-  const size_t bytes = 3 * NT * sizeof(float2);
+  const size_t bytes = (2 * padded(NT) + NT) * sizeof(float2);
   epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, odd, slot);
   return cudaGetLastError();
 }
@@ -556,7 +580,7 @@ cudaError_t launch_init_nt(const SurveyDev& s, const float* Gd, cudaStream_t st,
   const int npairs = (s.ncols + 1) / 2;
   int grid = num_sms * 4;
   if (grid > npairs) grid = npairs;
-  const size_t bytes = 2 * NT * sizeof(float2);
+  const size_t bytes = (padded(NT) + NT) * sizeof(float2);
   init_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, Gd);
   return cudaGetLastError();
 }

@@ -58,12 +58,29 @@ mk_status setup_device(int dev, void** out) {
   return MK_OK;
 }
 
+// FFT twiddles in the pass-by-pass layout of mk_fft.cu (radix-8 passes, then
+// radix 2 or 4): entry e of pass (R, Ns) at offset toff is
+// e^{-2 pi i r k / (Ns R)} with r = (e - toff) / Ns + 1, k = (e - toff) mod Ns.
 __global__ void twiddle_kernel(float2* tw, int nt) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= nt) return;
-  double s, c;
-  sincospi(-2.0 * (double)q / (double)nt, &s, &c);
-  tw[q] = make_float2((float)c, (float)s);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  int lg = 0;
+  while ((1 << lg) < nt) ++lg;
+  int Ns = 1, toff = 0;
+  for (int p = 0; p < lg / 3 + (lg % 3 ? 1 : 0); ++p) {
+    const int R = p < lg / 3 ? 8 : (lg % 3 == 1 ? 2 : 4);
+    if (e < toff + (R - 1) * Ns) {
+      const int r = (e - toff) / Ns + 1, k = (e - toff) % Ns;
+      const long long q = (long long)r * k * (nt / (Ns * R));
+      double sv, cv;
+      sincospi(-2.0 * (double)q / (double)nt, &sv, &cv);
+      tw[e] = make_float2((float)cv, (float)sv);
+      return;
+    }
+    toff += (R - 1) * Ns;
+    Ns *= R;
+  }
+  tw[e] = make_float2(0.f, 0.f);  // the table has nt - 1 entries; the last slot is unused
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
