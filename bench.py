@@ -250,30 +250,41 @@ def main_reference(args):
 
 # --------------------------------------------------------------------------- our arm
 class Runner:
-    """One plan on one workload; device-resident inputs; timed steps."""
+    """One plan over one or more surveys; device-resident inputs; timed steps.
 
-    def __init__(self, s, R, F, rprec, dev, local, timing=True):
+    ``items`` is a list of (survey, rprec); R of each survey is assembled on
+    the device (``synthetic.torch_gen``) unless ``R_dev`` gives it."""
+
+    def __init__(self, items, dev, local, R_dev=None, timing=True):
         import torch
         import synthetic as S
+        from synthetic.torch_gen import reflection_band_chunks
         from paper_2106_04649_gb300.api import Desc, Plan
         from paper_2106_04649_gb300 import _native as N
-        self.s, self.F, self.rprec = s, F, rprec
-        self.td = S.survey_td(s)
-        self.Gd = S.gd_traces(s, self.td, np.float32)
+        self.items = items
         flags = N.MK_FLAG_TIMING if timing else 0
-        self.desc = Desc(s.n, s.n, s.nt, F, s.dt, s.dx, s.fmax_hz, RPREC[rprec], flags)
+        descs = [Desc(s.n, s.n, s.nt, s.nfocal, s.dt, s.dx, s.fmax_hz or 0.0, RPREC[rp], flags) for s, rp in items]
         self.stream = torch.cuda.current_stream(dev)
-        self.plan = Plan([self.desc], device=local, stream=self.stream)
-        Rd = torch.from_numpy(R).to(dev)
-        self.plan.load_R(0, Rd)
+        self.plan = Plan(descs, device=local, stream=self.stream)
+        self.inputs = []
+        for i, (s, rp) in enumerate(items):
+            if R_dev is not None and len(items) == 1:
+                self.plan.load_R(i, R_dev)
+            else:
+                for w0, blk in reflection_band_chunks(s, dev, chunk=16):
+                    self.plan.load_R(i, blk.contiguous(), w_begin=w0)
+            td = S.survey_td(s)
+            Gd = S.gd_traces(s, td, np.float32)
+            self.inputs.append((torch.from_numpy(Gd).to(dev), torch.from_numpy(td).to(dev), s.eps, Gd, td))
         torch.cuda.synchronize()
-        del Rd
-        torch.cuda.empty_cache()
-        self.Gdd = torch.from_numpy(self.Gd).to(dev)
-        self.tdd = torch.from_numpy(self.td).to(dev)
+
+    @property
+    def F(self):
+        return sum(s.nfocal for s, _ in self.items)
 
     def step(self):
-        self.plan.set_Gd_window(0, self.Gdd, self.tdd, self.s.eps)
+        for i, (G, t, eps, _, _) in enumerate(self.inputs):
+            self.plan.set_Gd_window(i, G, t, eps)
         self.plan.iterate(NITER, energy=False)
 
     def timed(self, steps, warmup, clocks=None, dist=None):
@@ -337,8 +348,9 @@ def main_ours(args):
 
     s = survey(args.nfocal, world, rank)
     F = s.nfocal
-    R = S.reflection_band(s, dtype=np.complex64)  # the same R serves every focal set of this survey
-    run = Runner(s, R, F, args.rprec, dev, local)
+    from synthetic.torch_gen import reflection_band_torch
+    R_dev = reflection_band_torch(s, dev)  # the same R serves every focal set of this survey
+    run = Runner([(s, args.rprec)], dev, local, R_dev=R_dev)
     ms, st, clk = run.timed(args.steps, args.warmup, ClockSampler(local), dist if world > 1 else None)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -350,12 +362,13 @@ def main_ours(args):
     # end to end through the C ABI with host buffers (R, G_d, t_d in; energies and G out)
     e2e = None
     if not args.no_e2e:
-        Rh = torch.from_numpy(R).pin_memory()
-        Gh = torch.from_numpy(run.Gd).pin_memory()
-        th = torch.from_numpy(run.td).pin_memory()
+        Rh = R_dev.cpu().pin_memory()
+        Gd_h, td_h = run.inputs[0][3], run.inputs[0][4]
+        Gh = torch.from_numpy(Gd_h).pin_memory()
+        th = torch.from_numpy(td_h).pin_memory()
         Gout = torch.empty((1, F, s.n, s.nt), dtype=torch.float32).pin_memory()
         energy = torch.empty((NITER, F), dtype=torch.float64).pin_memory()
-        h2d = R.nbytes + run.Gd.nbytes + run.td.nbytes
+        h2d = Rh.numel() * 8 + Gd_h.nbytes + td_h.nbytes
         d2h = Gout.numel() * 4 + energy.numel() * 8
         h = run.plan.handle
 
@@ -391,13 +404,25 @@ def main_ours(args):
         for (vf, vp, vsteps) in [(64, "c64", 10), (64, "split", 20), (64, "split3", 20), (64, "cbf16", 20),
                                  (601, "split3", 5), (601, "split", 5), (601, "c64", 3)]:
             vs = survey(vf)
-            vr = Runner(vs, R, vf, vp, dev, local)
+            vr = Runner([(vs, vp)], dev, local, R_dev=R_dev)
             vms, vst, _ = vr.timed(vsteps, 2)
             vr.close()
             d = summarize(vs, vf, vp, vms, vsteps, vst)
             d.update({"nfocal": vf, "rprec": vp, "steps": vsteps})
             variants.append(d)
-        by = {(v["nfocal"], v["rprec"]): v["value"] for v in variants}
+        # batching: twelve uneven surveys in one plan (even: complex FP32, odd: 3-way split BF16)
+        del R_dev
+        torch.cuda.empty_cache()
+        bs = S.batching_surveys()
+        br = Runner([(x, "c64" if i % 2 == 0 else "split3") for i, x in enumerate(bs)], dev, local)
+        bms, bst, _ = br.timed(5, 2)
+        br.close()
+        variants.append({"workload": "batching: 12 surveys, n 201-1201, nt 1024-4096, 1-256 focal points, "
+                                     "even surveys c64, odd surveys split3, one plan", "nfocal": br.F,
+                         "value": br.F * 5 / (bms / 1e3), "ms_per_step": bms / 5,
+                         "contract_ms_total": bst["contract_ms"] / 5, "epilogue_ms_total": bst["epilogue_ms"] / 5,
+                         "gpu_launches_per_step": bst["launches"] / 5})
+        by = {(v["nfocal"], v["rprec"]): v["value"] for v in variants if "rprec" in v}
         for vf in (64, 601):
             for vp in ("split", "split3", "cbf16"):
                 if (vf, vp) in by and (vf, "c64") in by:

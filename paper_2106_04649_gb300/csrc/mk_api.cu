@@ -92,6 +92,9 @@ mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nt=%d must be a power of two in [32, 8192]", i, d.nt);
   if (!(d.dt > 0.0) || !(d.dx > 0.0) || !isfinite(d.dt) || !isfinite(d.dx))
     return fail(p, MK_ERR_ARG, "survey %d: dt and dx must be finite and > 0", i);
+  if (!mk::epilogue_fits(d.nt, band_bins(d)))
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nt=%d with %d kept bins exceeds the epilogue's shared memory", i,
+                d.nt, band_bins(d));
   if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT3_BF16)
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: unknown R storage precision %d", i, d.rprec);
   if ((int64_t)d.nsrc * d.nfocal > (int64_t)1 << 30)

@@ -296,73 +296,150 @@ __device__ __forceinline__ void pack_pair(const SurveyDev& s, float2* x, int t0,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Epilogue, blocked: a CTA takes a block of up to 2G consecutive traces
+// (G pairs).  Their band spectra are loaded from S into a trace-major
+// shared stage with one coalesced pass (consecutive threads read consecutive
+// traces of one frequency), the pairs are transformed one after the other,
+// each writing its new band spectra back into its own stage rows, and one
+// coalesced pass writes the block to Nw or to the 16-bit embedding.  The
+// stage's leading dimension ld is odd, so both the per-frequency and the
+// per-trace accesses of the stage are free of bank conflicts.
+
+__device__ __forceinline__ int stage_ld(int nw) { return nw | 1; }
+
+// Dynamic shared memory the epilogue may use (below the 227 KB per-CTA limit,
+// leaving room for its static shared memory).
+constexpr int kEpiSmemMax = 220 * 1024;
+
+// Hermitian pack of stage rows (a, b) into x (bins outside the band zero).
+template <int NT, int THREADS>
+__device__ __forceinline__ void pack_stage(const SurveyDev& s, float2* x, const float2* ra, const float2* rb,
+                                           bool hasb) {
+  for (int m = threadIdx.x; m <= NT / 2; m += THREADS) {
+    float2 X = make_float2(0.f, 0.f), Y = make_float2(0.f, 0.f);
+    if (m < s.nw) {
+      X = ra[m];
+      if (hasb) Y = rb[m];
+    }
+    if (m == 0 || m == NT / 2) {
+      X.y = 0.f;
+      Y.y = 0.f;
+    }
+    x[P(m)] = make_float2(X.x - Y.y, X.y + Y.x);
+    if (m > 0 && m < NT / 2) x[P(NT - m)] = make_float2(X.x + Y.y, Y.x - X.y);
+  }
+}
+
+// Forward transform of the pair in x (a + i b); band spectra into stage rows.
+template <int NT, int THREADS>
+__device__ __forceinline__ void forward_band_stage(const SurveyDev& s, float2* x, const float2* tw, float2* ra,
+                                                   float2* rb, bool hasb) {
+  fft_smem<NT, THREADS, false>(x, tw);
+  for (int m = threadIdx.x; m < s.nw; m += THREADS) {
+    const float2 zm = x[P(m)];
+    const float2 zc = cconj(x[P((NT - m) & (NT - 1))]);
+    ra[m] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
+    if (hasb) rb[m] = make_float2(0.5f * (zm.y - zc.y), -0.5f * (zm.x - zc.x));
+  }
+}
+
 template <int NT>
 __global__ void __launch_bounds__(threads_for(NT), NT <= 2048 ? 2 : 1)
-epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot) {
+epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot, int G) {
   constexpr int THREADS = threads_for(NT);
   constexpr int PJ = NT / THREADS;  // samples per thread
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);  // inverse transform
   float2* y = x + padded(NT);                       // N_i pair for the forward transform
   float2* tw = y + padded(NT);
+  float2* stage = tw + NT;                          // [2G][ld] band spectra of the block
+  const int ld = stage_ld(s.nw);
   __shared__ double red[2 * (THREADS / 32)];
   __shared__ int s_last;
 
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
   __syncthreads();
 
-  const int npairs = (s.ncols + 1) / 2;
+  const int bt = 2 * G;  // traces per block
+  const int nblocks = (s.ncols + bt - 1) / bt;
   const float inv = s.inv_nt;
   float* __restrict__ f1 = odd ? s.f1p : s.f1m;
-  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
-    const int t0 = 2 * p;
-    const bool hasb = t0 + 1 < s.ncols;
-    // 1. Hermitian pack of the two band spectra (bins outside the band are zero)
-    pack_pair<NT, THREADS>(s, x, t0, hasb);
-    __syncthreads();
-    // 2. inverse transform: x[j] = nt * (s_a(j) + i s_b(j))
-    fft_smem<NT, THREADS, true>(x, tw);
-    // 3. reverse, negate, mute; accumulate f1 (window samples only); N_i into y
-    const int La = s.L[t0];
-    const int Lb = hasb ? s.L[t0 + 1] : 0;
-    const int64_t ba = field_offset(s, t0);
-    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
-    double ea = 0.0, eb = 0.0;
-    float ha[PJ], hb[PJ];
-#pragma unroll
-    for (int q = 0; q < PJ; ++q) {  // all loads first: one round trip
-      const int j = threadIdx.x + q * THREADS;
-      const int d = j < NT - j ? j : NT - j;
-      ha[q] = d < La ? f1[ba + j] : 0.f;
-      hb[q] = (hasb && d < Lb) ? f1[bb + j] : 0.f;
-    }
-#pragma unroll
-    for (int q = 0; q < PJ; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      const int d = j < NT - j ? j : NT - j;  // |signed index|
-      const float2 zj = x[P(j)];
-      const float2 zr = x[P((NT - j) & (NT - 1))];
-      const float sa = zj.x * inv, sb = zj.y * inv;
-      const float na = d < La ? -(zr.x * inv) : 0.f;
-      const float nb = d < Lb ? -(zr.y * inv) : 0.f;
-      y[P(j)] = make_float2(na, nb);
-      if (d < La) {
-        f1[ba + j] = ha[q] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
-        ea += (double)na * (double)na;
-      }
-      if (d < Lb) {
-        f1[bb + j] = hb[q] + (odd ? nb : sb);
-        eb += (double)nb * (double)nb;
-      }
+  for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    const int tb = blk * bt;
+    const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
+    // 1. the block's band spectra, one coalesced pass
+    for (int idx = threadIdx.x; idx < s.nw * ntr; idx += THREADS) {
+      const int m = idx / ntr, c = idx - (idx / ntr) * ntr;
+      stage[c * ld + m] = __ldg(s.S + (int64_t)m * s.s_stride + tb + c);
     }
     __syncthreads();
-    // 4. forward transform of N_i, band spectra to Nw
-    forward_band_pair<NT, THREADS>(s, y, tw, t0, hasb);
-    // 5. per-trace energies
-    block_sum2<THREADS>(ea, eb, red);
-    if (threadIdx.x == 0) {
-      s.Epart[t0] = ea;
-      if (hasb) s.Epart[t0 + 1] = eb;
+    for (int q = 0; 2 * q < ntr; ++q) {
+      const int t0 = tb + 2 * q;
+      const bool hasb = 2 * q + 1 < ntr;
+      float2* ra = stage + (2 * q) * ld;
+      float2* rb = ra + ld;
+      // 2. Hermitian pack (bins outside the band are zero), inverse transform
+      pack_stage<NT, THREADS>(s, x, ra, rb, hasb);
+      __syncthreads();
+      fft_smem<NT, THREADS, true>(x, tw);
+      // 3. reverse, negate, mute; accumulate f1 (window samples only); N_i into y
+      const int La = s.L[t0];
+      const int Lb = hasb ? s.L[t0 + 1] : 0;
+      const int64_t ba = field_offset(s, t0);
+      const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+      double ea = 0.0, eb = 0.0;
+      float ha[PJ], hb[PJ];
+#pragma unroll
+      for (int k = 0; k < PJ; ++k) {  // all loads first: one round trip
+        const int j = threadIdx.x + k * THREADS;
+        const int d = j < NT - j ? j : NT - j;
+        ha[k] = d < La ? f1[ba + j] : 0.f;
+        hb[k] = (hasb && d < Lb) ? f1[bb + j] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < PJ; ++k) {
+        const int j = threadIdx.x + k * THREADS;
+        const int d = j < NT - j ? j : NT - j;  // |signed index|
+        const float2 zj = x[P(j)];
+        const float2 zr = x[P((NT - j) & (NT - 1))];
+        const float sa = zj.x * inv, sb = zj.y * inv;
+        const float na = d < La ? -(zr.x * inv) : 0.f;
+        const float nb = d < Lb ? -(zr.y * inv) : 0.f;
+        y[P(j)] = make_float2(na, nb);
+        if (d < La) {
+          f1[ba + j] = ha[k] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
+          ea += (double)na * (double)na;
+        }
+        if (d < Lb) {
+          f1[bb + j] = hb[k] + (odd ? nb : sb);
+          eb += (double)nb * (double)nb;
+        }
+      }
+      __syncthreads();
+      // 4. forward transform of N_i, band spectra into the stage rows of this pair
+      forward_band_stage<NT, THREADS>(s, y, tw, ra, rb, hasb);
+      // 5. per-trace energies
+      block_sum2<THREADS>(ea, eb, red);
+      if (threadIdx.x == 0) {
+        s.Epart[t0] = ea;
+        if (hasb) s.Epart[t0 + 1] = eb;
+      }
+      __syncthreads();
+    }
+    // 6. the block's new band spectra, one coalesced pass
+    for (int idx = threadIdx.x; idx < s.nw * ntr; idx += THREADS) {
+      const int m = idx / ntr, c = idx - (idx / ntr) * ntr;
+      const float2 v = stage[c * ld + m];
+      const int t = tb + c;
+      if (s.rprec == 0) {
+        const int f = t / s.ns, k = t - (t / s.ns) * s.ns;
+        s.Nw[(int64_t)m * s.nw_stride + (int64_t)f * s.r_pad + k] = v;
+      } else if (s.rprec == 2) {
+        store_embedding<false>(s, m, t, v.x, v.y);
+      } else {
+        store_embedding<true>(s, m, t, v.x, v.y);
+      }
     }
     __syncthreads();
   }
@@ -536,8 +613,8 @@ __global__ void green_kernel(SurveyDev s, float* __restrict__ out) {
 template <int NT>
 cudaError_t set_attrs() {
   constexpr int one = (padded(NT) + NT) * (int)sizeof(float2);
-  constexpr int two = (2 * padded(NT) + NT) * (int)sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, two);
+  // the epilogue's stage grows with the band: allow the per-CTA maximum
+  cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEpiSmemMax);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
   if (e != cudaSuccess) return e;
@@ -564,14 +641,29 @@ cudaError_t launch_spec_nt(const SurveyDev& s, const float* src, cudaStream_t st
   return cudaGetLastError();
 }
 
+// Pairs per epilogue block: as many as keep two CTAs per SM (<= 113 KB of
+// shared memory each), at most 4, at least 1.
+template <int NT>
+int epi_pairs(int nw, size_t* bytes) {
+  const size_t base = (2 * padded(NT) + NT) * sizeof(float2);
+  const size_t ld = (size_t)(nw | 1);
+  int G = 4;
+  while (G > 1 && base + 2 * G * ld * sizeof(float2) > 113 * 1024) --G;
+  *bytes = base + 2 * G * ld * sizeof(float2);
+  return G;
+}
+
 template <int NT>
 cudaError_t launch_epi_nt(const SurveyDev& s, int odd, double* slot, cudaStream_t st, int num_sms) {
-  const int npairs = (s.ncols + 1) / 2;
-  const int per_sm = NT >= 4096 ? 2 : 4;
-  int grid = num_sms * per_sm;
-  if (grid > npairs) grid = npairs;
-  const size_t bytes = (2 * padded(NT) + NT) * sizeof(float2);
-  epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, odd, slot);
+  size_t bytes = 0;
+  int G = epi_pairs<NT>(s.nw, &bytes);
+  // few traces: smaller blocks so that every SM gets work
+  while (G > 1 && (s.ncols + 2 * G - 1) / (2 * G) < 2 * num_sms) --G;
+  bytes = (2 * padded(NT) + NT) * sizeof(float2) + 2 * (size_t)G * (size_t)(s.nw | 1) * sizeof(float2);
+  const int nblocks = (s.ncols + 2 * G - 1) / (2 * G);
+  int grid = num_sms * 2;
+  if (grid > nblocks) grid = nblocks;
+  epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, odd, slot, G);
   return cudaGetLastError();
 }
 
@@ -610,6 +702,18 @@ cudaError_t prepare_kernels() {
   MK_ATTR(4096) MK_ATTR(8192)
 #undef MK_ATTR
   return cudaSuccess;
+}
+
+bool epilogue_fits(int nt, int nw) {
+  size_t bytes = 0;
+  switch (nt) {
+#define MK_FIT(N) \
+  case N: epi_pairs<N>(nw, &bytes); break;
+    MK_FIT(32) MK_FIT(64) MK_FIT(128) MK_FIT(256) MK_FIT(512) MK_FIT(1024) MK_FIT(2048) MK_FIT(4096) MK_FIT(8192)
+#undef MK_FIT
+    default: return false;
+  }
+  return bytes <= (size_t)kEpiSmemMax;
 }
 
 cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,

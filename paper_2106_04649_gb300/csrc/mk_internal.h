@@ -60,6 +60,7 @@ cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t ro
                                int num_sms);
 cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
                             int num_sms);
+bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the per-CTA limit
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);
 cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms);  // band spectrum of a field
 cudaError_t launch_inverse(const SurveyDev& s, float* dst, int mode, cudaStream_t st, int num_sms);

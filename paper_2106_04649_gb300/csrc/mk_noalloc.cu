@@ -113,6 +113,7 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
     const double q = floor(d->fmax_hz * d->nt * d->dt);
     v.nw = (q >= d->nt / 2 ? d->nt / 2 : (int)q) + 1;
   }
+  if (!mk::epilogue_fits(d->nt, v.nw)) return set_err(MK_ERR_UNSUPPORTED, "nt and band exceed the epilogue's shared memory");
   v.r_pad = (d->nrec + 31) / 32 * 32;
   v.ncols = v.ns * v.F;
   v.s_stride = ((int64_t)v.ncols + 1 + 3) / 4 * 4;

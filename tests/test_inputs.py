@@ -111,3 +111,12 @@ def test_calibration_bounds_operator_norm():
     worst = max(np.linalg.norm(c * R[m], 2) for m in range(0, R.shape[0], 7))
     assert worst <= s.calibrate
     assert worst > 0.5 * s.calibrate  # and the bound is not vacuous
+
+
+def test_torch_assembly_matches_host_generator():
+    torch = pytest.importorskip("torch")
+    from synthetic.torch_gen import reflection_band_torch
+    for s in (S.tiny_survey(), S.batching_surveys()[0]):
+        ref = S.reflection_band(s, dtype=np.complex128)
+        got = reflection_band_torch(s, "cpu", dtype=torch.complex128).numpy()
+        assert np.array_equal(got, ref)
