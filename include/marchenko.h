@@ -93,7 +93,9 @@ typedef enum {
 #define MK_F_F2P  (1u << 3) /* f2p                                         */
 #define MK_F_PMIN (1u << 4) /* pmin                                        */
 #define MK_F_G    (1u << 5) /* G = f2p(-t) + pmin(t)                       */
-#define MK_F_ALL  (0x3Fu)
+#define MK_F_GMINUS (1u << 6) /* G^- = synthesis(f1plus) - f1min          */
+#define MK_F_GPLUS  (1u << 7) /* G^+ = f1plus(-t) - synthesis(f1min(-t))  */
+#define MK_F_ALL  (0xFFu)
 
 /* mk_desc.flags */
 #define MK_FLAG_TIMING (1u << 0) /* record CUDA events around every kernel   */
@@ -192,12 +194,28 @@ mk_status mk_iterate(mk_plan_t plan, int32_t niter, double* energy);
  * f1min only; N_last, f2p, pmin and G are formed on the GPU when fetched
  * (f2p = f1plus - f1min(-t); pmin = synthesis of f2p - N_last, one extra
  * contraction; G = f2p(-t) + pmin), which is exact algebra of Algorithm 1.
+ * MK_F_GMINUS is the up-going Green's function of Algorithm 1 (one extra
+ * synthesis of f1plus after the loop, minus f1min); MK_F_GPLUS the
+ * down-going one, f1plus(-t) minus the synthesis of f1min(-t) (Theory: each
+ * component needs one extra synthesis; the G^+ formula is a reading, and
+ * G - G^+ - G^- equals minus the synthesis of the last N_i).
  *   out: host (dst_on_device = 0) or device (1) buffer of out_bytes >=
  *        popcount(mask) * nfocal * nsrc * nt * 4.
  * Errors: MK_ERR_ARG, MK_ERR_STATE (G_d not set), MK_ERR_CUDA.
  */
 mk_status mk_fetch_fields(mk_plan_t plan, int32_t survey, uint32_t mask, float* out,
                           size_t out_bytes, int32_t dst_on_device);
+
+/*
+ * mk_image - double-focusing image of each focal point of one survey: the
+ * zero-time sample of the time convolution of G^- with f1plus, integrated
+ * over the surface positions (Theory section; Algorithm 1, "imaging"):
+ *     image(f) = dx dt sum_k sum_j G^-(f, x_k, t_j) f1plus(f, x_k, -t_j),
+ * accumulated in FP64 in a fixed order.  Forms G^- if needed (one synthesis).
+ *   image: double [nfocal], host (dst_on_device = 0) or device (1).
+ * Errors: MK_ERR_ARG, MK_ERR_STATE (G_d not set), MK_ERR_CUDA.
+ */
+mk_status mk_image(mk_plan_t plan, int32_t survey, double* image, int32_t dst_on_device);
 
 /*
  * mk_set_fields - resume a series from saved fields (checkpoint / restart;

@@ -216,3 +216,29 @@ def direct_solution(Rw: np.ndarray, Gd: np.ndarray, td: np.ndarray, eps: float, 
         yf[win] = yw
         y[f] = yf.reshape(n, nt)
     return y, Nm1 + y
+
+
+# ---------------------------------------------------------------------------
+# After the iterations: up/down-going Green's functions and the image
+# ---------------------------------------------------------------------------
+
+def green_minus(Rw: np.ndarray, f1plus: np.ndarray, f1min: np.ndarray, c: float) -> np.ndarray:
+    """G^-(t) = synthesis(f1plus)(t) - f1min(t): the extra synthesis after the
+    loop in Algorithm 1 ("cuda_synthesis(Refl, f1plus, iRN); Gmin = iRN - f1min")."""
+    return synthesis(Rw, f1plus, c) - f1min
+
+
+def green_plus(Rw: np.ndarray, f1plus: np.ndarray, f1min: np.ndarray, c: float) -> np.ndarray:
+    """G^+(t) = f1plus(-t) - synthesis(f1min(-t))(t): the down-going part with
+    its own extra synthesis (Theory section, citing the coupled Marchenko
+    representations; the formula is a reading: G^+(-t) = f1plus(t) minus the
+    correlation of R with f1min).  With the readings used here
+    G - G^+ - G^- = -synthesis(N_last) exactly."""
+    return reverse_time(f1plus) - synthesis(Rw, reverse_time(f1min), c)
+
+
+def image(Gmin: np.ndarray, f1plus: np.ndarray, dx: float, dt: float) -> np.ndarray:
+    """Double-focusing image per focal point: the zero-time sample of the
+    time convolution of G^- with f1plus, integrated over the surface
+    positions (Theory section): dx dt sum_k sum_j G^-(k, j) f1plus(k, -j)."""
+    return dx * dt * np.sum(Gmin * reverse_time(f1plus), axis=(1, 2))

@@ -13,6 +13,8 @@ from ._native import (  # noqa: F401
     MK_F_F1P,
     MK_F_F2P,
     MK_F_G,
+    MK_F_GMINUS,
+    MK_F_GPLUS,
     MK_F_N,
     MK_F_PMIN,
     MK_FLAG_TIMING,

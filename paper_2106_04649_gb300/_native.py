@@ -15,8 +15,8 @@ MK_OK, MK_ERR_ARG, MK_ERR_STATE, MK_ERR_OOM, MK_ERR_CUDA, MK_ERR_TIMEOUT, MK_ERR
 STATUS_NAMES = ["MK_OK", "MK_ERR_ARG", "MK_ERR_STATE", "MK_ERR_OOM", "MK_ERR_CUDA", "MK_ERR_TIMEOUT",
                 "MK_ERR_UNSUPPORTED"]
 MK_R_C64, MK_R_CBF16, MK_R_CF16, MK_R_SPLIT_BF16, MK_R_SPLIT3_BF16 = range(5)
-MK_F_N, MK_F_F1P, MK_F_F1M, MK_F_F2P, MK_F_PMIN, MK_F_G = (1 << i for i in range(6))
-MK_F_ALL = 0x3F
+MK_F_N, MK_F_F1P, MK_F_F1M, MK_F_F2P, MK_F_PMIN, MK_F_G, MK_F_GMINUS, MK_F_GPLUS = (1 << i for i in range(8))
+MK_F_ALL = 0xFF
 MK_FLAG_TIMING = 1
 
 
@@ -61,6 +61,7 @@ _SIGS = {
                                      ctypes.c_int32]),
     "mk_destroy": (ctypes.c_int, [_P]),
     "mk_last_error": (ctypes.c_char_p, [_P]),
+    "mk_image": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,
                                       _P]),
 }

@@ -94,7 +94,13 @@ class Plan:
         return e
 
     # -- outputs --------------------------------------------------------------
-    def fetch_fields(self, survey: int, mask: int = N.MK_F_ALL, out=None):
+    def image(self, survey: int):
+        """Double-focusing image [F] (zero lag of G^- * f1plus)."""
+        out = np.zeros(self.descs[survey].nfocal, dtype=np.float64)
+        B.mk_image(self.handle, survey, out.ctypes.data, False)
+        return out
+
+    def fetch_fields(self, survey: int, mask: int = 0x3F, out=None):
         d = self.descs[survey]
         nf = bin(mask).count("1")
         shape = (nf, d.nfocal, d.nsrc, d.nt)

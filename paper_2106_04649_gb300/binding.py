@@ -68,6 +68,10 @@ def mk_set_fields(plan: int, survey: int, mask: int, data: int, nbytes: int, ite
     _check(N.load().mk_set_fields(plan, survey, mask, data, nbytes, iteration, int(src_on_device)), plan)
 
 
+def mk_image(plan: int, survey: int, image: int, dst_on_device: bool) -> None:
+    _check(N.load().mk_image(plan, survey, image, int(dst_on_device)), plan)
+
+
 def mk_get_stats(plan: int, reset: bool = False) -> dict:
     st = N.MkStats()
     _check(N.load().mk_get_stats(plan, ctypes.byref(st), int(reset)), plan)

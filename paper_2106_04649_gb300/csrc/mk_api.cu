@@ -32,6 +32,7 @@ struct Survey {
   int iter = 0;
   bool n_in_field = true;   // fN holds the last N (else it follows from S)
   bool derived_valid = false;  // f2p and pmin formed since the last change
+  bool gm_valid = false, gp_valid = false;  // G^- and G^+ formed since the last change
   size_t offset = 0, bytes = 0;  // carving inside the workspace
 };
 
@@ -150,6 +151,8 @@ size_t layout(Survey& sv, char* base) {
   v.f2p = reinterpret_cast<float*>(take(field));
   v.pmin = reinterpret_cast<float*>(take(field));
   v.scratch = reinterpret_cast<float*>(take(field));
+  v.gm = reinterpret_cast<float*>(take(field));
+  v.gp = reinterpret_cast<float*>(take(field));
   v.L = reinterpret_cast<int*>(take((size_t)(v.ncols + 1) * sizeof(int)));
   v.td = reinterpret_cast<double*>(take((size_t)v.ncols * sizeof(double)));
   v.Epart = reinterpret_cast<double*>(take((size_t)(v.ncols + 1) * sizeof(double)));
@@ -236,16 +239,62 @@ TimedPair* next_pair(mk_plan_t p, int kind) {
 //   f2p = f1plus - f1min(-t),  pmin = synthesis(f2p - N_last).
 // The pmin synthesis reuses the contraction; the band spectrum of N_last is
 // restored afterwards so the series continues unchanged.
+// One plain synthesis (Eq. 1 before the mute) of a field into dst: band
+// spectrum, contraction, inverse transform.  Overwrites Nw and S.
+mk_status synthesize(mk_plan_t p, Survey& sv, const float* src, float* dst) {
+  mk::SurveyDev& v = sv.dev;
+  int nl = 0;
+  MK_CUDA(p, mk::launch_spectrum(v, src, p->stream, p->num_sms));
+  MK_CUDA(p, mk::launch_contract(v, sv.umma, p->stream, p->num_sms, &nl));
+  MK_CUDA(p, mk::launch_inverse(v, dst, 1, p->stream, p->num_sms));
+  p->stats.launches += 2 + nl;
+  p->stats.other_launches += 2 + nl;
+  return MK_OK;
+}
+
+// G^- = synthesis(f1plus) - f1min (Algorithm 1, after the loop) and
+// G^+ = f1plus(-t) - synthesis(f1min(-t)), each one extra synthesis.
+mk_status materialize_up_down(mk_plan_t p, Survey& sv, uint32_t mask) {
+  mk::SurveyDev& v = sv.dev;
+  mk_status st;
+  bool touched = false;
+  if ((mask & MK_F_GMINUS) && !sv.gm_valid) {
+    if ((st = synthesize(p, sv, v.f1p, v.scratch)) != MK_OK) return st;
+    MK_CUDA(p, mk::launch_lincomb(v, v.gm, v.scratch, 0, 1.f, v.f1m, 0, -1.f, p->stream, p->num_sms));
+    p->stats.launches++;
+    p->stats.other_launches++;
+    sv.gm_valid = touched = true;
+  }
+  if ((mask & MK_F_GPLUS) && !sv.gp_valid) {
+    MK_CUDA(p, mk::launch_lincomb(v, v.scratch, v.f1m, 1, 1.f, nullptr, 0, 0.f, p->stream, p->num_sms));
+    if ((st = synthesize(p, sv, v.scratch, v.scratch)) != MK_OK) return st;
+    MK_CUDA(p, mk::launch_lincomb(v, v.gp, v.f1p, 1, 1.f, v.scratch, 0, -1.f, p->stream, p->num_sms));
+    p->stats.launches += 2;
+    p->stats.other_launches += 2;
+    sv.gp_valid = touched = true;
+  }
+  if (touched) {  // restore the band spectrum of N_last for the next iteration
+    MK_CUDA(p, mk::launch_spectrum(v, v.fN, p->stream, p->num_sms));
+    p->stats.launches++;
+    p->stats.other_launches++;
+  }
+  return MK_OK;
+}
+
 mk_status materialize(mk_plan_t p, Survey& sv, uint32_t mask) {
   mk::SurveyDev& v = sv.dev;
   const bool need_pmin = mask & (MK_F_PMIN | MK_F_G);
   const bool need_f2p = need_pmin || (mask & MK_F_F2P);
-  const bool need_n = need_f2p || (mask & MK_F_N);
+  const bool need_n = need_f2p || (mask & (MK_F_N | MK_F_GMINUS | MK_F_GPLUS));
   if (need_n && !sv.n_in_field) {
     MK_CUDA(p, mk::launch_inverse(v, v.fN, 0, p->stream, p->num_sms));
     p->stats.launches++;
     p->stats.other_launches++;
     sv.n_in_field = true;
+  }
+  if (mask & (MK_F_GMINUS | MK_F_GPLUS)) {
+    mk_status st = materialize_up_down(p, sv, mask);
+    if (st != MK_OK) return st;
   }
   if (!need_f2p || sv.derived_valid) return MK_OK;
   MK_CUDA(p, mk::launch_f2p(v, v.scratch, p->stream, p->num_sms));  // f2p, and f2p - N into scratch
@@ -465,7 +514,7 @@ mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const d
   sv->ready = true;
   sv->iter = 0;
   sv->n_in_field = true;
-  sv->derived_valid = false;
+  sv->derived_valid = sv->gm_valid = sv->gp_valid = false;
   return MK_OK;
 }
 
@@ -500,7 +549,7 @@ mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
         p->stats.epilogue_launches++;
         sv.iter++;
         sv.n_in_field = false;
-        sv.derived_valid = false;
+        sv.derived_valid = sv.gm_valid = sv.gp_valid = false;
       }
     }
     if (energy) {
@@ -536,9 +585,9 @@ mk_status mk_fetch_fields(mk_plan_t p, int32_t survey, uint32_t mask, float* out
   if (out_bytes < need) return fail(p, MK_ERR_ARG, "output of %zu bytes, %zu needed", out_bytes, need);
   if ((st = materialize(p, *sv, mask)) != MK_OK) return st;
   const cudaMemcpyKind kind = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  const float* src[6] = {v.fN, v.f1p, v.f1m, v.f2p, v.pmin, nullptr};
+  const float* src[8] = {v.fN, v.f1p, v.f1m, v.f2p, v.pmin, nullptr, v.gm, v.gp};
   float* o = out;
-  for (int b = 0; b < 6; ++b) {
+  for (int b = 0; b < 8; ++b) {
     if (!(mask & (1u << b))) continue;
     if (b == 5) {
       float* gdst = dst_on_device ? o : v.scratch;
@@ -590,7 +639,30 @@ mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float*
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   sv->iter = iteration;
   sv->n_in_field = true;
-  sv->derived_valid = false;
+  sv->derived_valid = sv->gm_valid = sv->gp_valid = false;
+  return MK_OK;
+}
+
+mk_status mk_image(mk_plan_t p, int32_t survey, double* image, int32_t dst_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!image) return fail(p, MK_ERR_ARG, "null output pointer");
+  if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
+  if ((st = materialize(p, *sv, MK_F_GMINUS)) != MK_OK) return st;
+  const mk::SurveyDev& v = sv->dev;
+  double* dst = image;
+  if (!dst_on_device) dst = v.Epart;  // staging: the per-trace energy buffer holds >= F doubles
+  MK_CUDA(p, mk::launch_image(v, v.gm, sv->d.dx * sv->d.dt, dst, p->stream));
+  p->stats.launches++;
+  p->stats.other_launches++;
+  if (!dst_on_device) {
+    MK_CUDA(p, cudaMemcpyAsync(image, dst, (size_t)v.F * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    MK_CUDA(p, cudaStreamSynchronize(p->stream));
+    if ((st = check_device_errors(p)) != MK_OK) return st;
+  }
   return MK_OK;
 }
 

@@ -599,6 +599,48 @@ __global__ void f2p_kernel(SurveyDev s, float* __restrict__ diff) {
   }
 }
 
+// out = alpha * A(+-t) + beta * B(+-t) per trace (revA / revB: read at -t).
+__global__ void lincomb_kernel(SurveyDev s, float* __restrict__ out, const float* __restrict__ A, int revA,
+                               float alpha, const float* __restrict__ B, int revB, float beta) {
+  const int64_t total = (int64_t)s.F * s.ns * s.nt;
+  const int mask = s.nt - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i & mask);
+    const int64_t base = i - j;
+    const int jr = (s.nt - j) & mask;
+    float v = alpha * A[revA ? base + jr : i];
+    if (B) v += beta * B[revB ? base + jr : i];
+    out[i] = v;
+  }
+}
+
+// Double-focusing image per focal point: zero-time sample of the time
+// convolution of G^- with f1plus, integrated over positions,
+// image(f) = dx dt sum_k sum_j G^-(f, k, j) f1plus(f, k, -j); FP64
+// accumulation in a fixed order (one CTA per focal point).
+__global__ void image_kernel(SurveyDev s, const float* __restrict__ gm, double scale, double* __restrict__ out) {
+  const int f = blockIdx.x;
+  const int64_t n = (int64_t)s.ns * s.nt;
+  const int mask = s.nt - 1;
+  const float* g = gm + (int64_t)f * n;
+  const float* p = s.f1p + (int64_t)f * n;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const int j = (int)(i & mask);
+    acc += (double)g[i] * (double)p[i - j + ((s.nt - j) & mask)];
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[f] = scale * t;
+  }
+}
+
 __global__ void green_kernel(SurveyDev s, float* __restrict__ out) {
   const int64_t total = (int64_t)s.F * s.ns * s.nt;
   const int mask = s.nt - 1;
@@ -748,6 +790,17 @@ cudaError_t launch_inverse(const SurveyDev& s, float* dst, int mode, cudaStream_
 
 cudaError_t launch_f2p(const SurveyDev& s, float* diff, cudaStream_t st, int num_sms) {
   f2p_kernel<<<num_sms * 8, 256, 0, st>>>(s, diff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lincomb(const SurveyDev& s, float* out, const float* A, int revA, float alpha, const float* B,
+                           int revB, float beta, cudaStream_t st, int num_sms) {
+  lincomb_kernel<<<num_sms * 8, 256, 0, st>>>(s, out, A, revA, alpha, B, revB, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image(const SurveyDev& s, const float* gm, double scale, double* out, cudaStream_t st) {
+  image_kernel<<<s.F, 512, 0, st>>>(s, gm, scale, out);
   return cudaGetLastError();
 }
 

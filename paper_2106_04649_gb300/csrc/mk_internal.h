@@ -42,6 +42,8 @@ struct SurveyDev {
   float* f2p;
   float* pmin;
   float* scratch;   // [F][ns][nt] staging (G_d upload, G for host output)
+  float* gm;        // [F][ns][nt] G^- (formed on request)
+  float* gp;        // [F][ns][nt] G^+ (formed on request)
   int* L;           // [ncols] window half-lengths
   double* td;       // [F][ns] staging of t_d uploaded from the host
   double* Epart;    // [ncols + 1] per-trace energies
@@ -69,6 +71,9 @@ cudaError_t launch_load_rows(const float2* src, float2* dst, int64_t rows, int n
                              int num_sms);
 cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st);
 cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms);
+cudaError_t launch_lincomb(const SurveyDev& s, float* out, const float* A, int revA, float alpha, const float* B,
+                           int revB, float beta, cudaStream_t st, int num_sms);
+cudaError_t launch_image(const SurveyDev& s, const float* gm, double scale, double* out, cudaStream_t st);
 cudaError_t prepare_kernels();  // one-time function attributes (large dynamic smem)
 cudaError_t prepare_contract();  // called by prepare_kernels
 cudaError_t prepare_gemv();

@@ -252,3 +252,34 @@ def test_per_iteration_from_identical_inputs(case, tiny_inputs):
             assert err <= TOL_ITER, f"{case} iter {i} {name}: {err:.3e}"
         prev = hist[i]
     p.close()
+
+
+@pytest.mark.parametrize("rprec", [0, 4])
+def test_green_up_down_and_image(tiny_inputs, rprec):
+    # G^- (Algorithm 1 after the loop), G^+ and the double-focusing image vs the oracle
+    from paper_2106_04649_gb300 import _native as N
+    from paper_2106_04649_gb300.api import Plan
+    s, R64, td, Gd64 = tiny_inputs
+    R = R64.astype(np.complex64)
+    Gd = Gd64.astype(np.float32)
+    c = s.dx * s.dt
+    st = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 8)
+    gm = M.green_minus(R.astype(np.complex128), st.f1plus, st.f1min, c)
+    gp = M.green_plus(R.astype(np.complex128), st.f1plus, st.f1min, c)
+    img = M.image(gm, st.f1plus, s.dx, s.dt)
+    p = Plan([desc_for(s, rprec=rprec)])
+    p.load_R(0, R)
+    p.set_Gd_window(0, Gd, td, s.eps)
+    p.iterate(8)
+    f = p.fetch_fields(0, N.MK_F_GMINUS | N.MK_F_GPLUS | N.MK_F_G | N.MK_F_F1P)
+    assert rel_l2(f[0], gm) <= 1e-5
+    assert rel_l2(f[1], gp) <= 1e-5
+    assert rel_l2(f[2], M.total_green(st.f2p, st.pmin)) <= 1e-5
+    # forming G^+ / G^- must not disturb the series: continue and compare again
+    im = p.image(0)
+    assert abs(im[0] - img[0]) <= 1e-5 * abs(img[0])
+    p.iterate(2)
+    st2 = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 10)
+    f2 = p.fetch_fields(0)
+    _compare(f2, st2, TOL_ITER, TOL_N, "after G+/G- and 2 more iterations")
+    p.close()

@@ -398,3 +398,43 @@ def test_tiny_energy_regression(tiny_inputs):
     s, R, td, Gd = tiny_inputs
     st = M.run(R, Gd, td, s.eps, s.dt, s.dx, 16)
     assert np.allclose(np.array(st.energy)[:, 0], ref[:, 1], rtol=1e-10, atol=0)
+
+
+def test_green_up_down_sum_identity(tiny_inputs):
+    # G - G^+ - G^- = -synthesis(N_last): pins the signs and reversals of G^+ against G's reading
+    s, R, td, Gd = tiny_inputs
+    c = s.dx * s.dt
+    for niter in (3, 8):
+        st = M.run(R, Gd, td, s.eps, s.dt, s.dx, niter)
+        G = M.total_green(st.f2p, st.pmin)
+        Gm = M.green_minus(R, st.f1plus, st.f1min, c)
+        Gp = M.green_plus(R, st.f1plus, st.f1min, c)
+        assert rel_l2(G - Gp - Gm, -M.synthesis(R, st.N, c)) < 1e-12
+
+
+def test_green_minus_definition_spikes():
+    # 1D spikes: G^- = R * f1plus - f1min exactly (exact rational algebra)
+    niter = 5
+    hist = exact_spike_run(SPIKES, TD, EPS, NT, niter)
+    h = hist[-1]
+    gm_exact = sp_add(sp_conv(SPIKES, h["f1plus"], NT), h["f1min"], -1)
+    Rw, Gd, td = spike_oracle_inputs(SPIKES, TD, NT)
+    st = M.run(Rw, Gd, td, float(EPS), 1.0, 1.0, niter, c=1.0)
+    gm = M.green_minus(Rw, st.f1plus, st.f1min, 1.0)
+    assert np.max(np.abs(gm[0, 0] - sp_dense(gm_exact, NT))) < 1e-13
+    # image = zero lag of G^- * f1plus, by the exact spike product
+    img_exact = sum(v * h["f1plus"].get((-t) % NT, 0) for t, v in gm_exact.items())
+    assert abs(M.image(gm, st.f1plus, 1.0, 1.0)[0] - float(img_exact)) < 1e-13
+
+
+def test_image_brute_force(tiny_inputs):
+    s, R, td, Gd = tiny_inputs
+    st = M.run(R, Gd, td, s.eps, s.dt, s.dx, 4)
+    Gm = M.green_minus(R, st.f1plus, st.f1min, s.dx * s.dt)
+    nt = s.nt
+    acc = 0.0
+    for k in range(0, s.n, 25):
+        for j in range(nt):
+            acc += Gm[0, k, j] * st.f1plus[0, k, (nt - j) % nt]
+    sub = Gm[:, ::25], st.f1plus[:, ::25]
+    assert abs(M.image(*sub, s.dx, s.dt)[0] - s.dx * s.dt * acc) < 1e-12 * abs(acc) * s.dx * s.dt + 1e-300
