@@ -255,14 +255,14 @@ class Runner:
     ``items`` is a list of (survey, rprec); R of each survey is assembled on
     the device (``synthetic.torch_gen``) unless ``R_dev`` gives it."""
 
-    def __init__(self, items, dev, local, R_dev=None, timing=True):
+    def __init__(self, items, dev, local, R_dev=None, timing=True, graph=False):
         import torch
         import synthetic as S
         from synthetic.torch_gen import reflection_band_chunks
         from paper_2106_04649_gb300.api import Desc, Plan
         from paper_2106_04649_gb300 import _native as N
         self.items = items
-        flags = N.MK_FLAG_TIMING if timing else 0
+        flags = (N.MK_FLAG_TIMING if timing else 0) | (N.MK_FLAG_GRAPH if graph else 0)
         descs = [Desc(s.n, s.n, s.nt, s.nfocal, s.dt, s.dx, s.fmax_hz or 0.0, RPREC[rp], flags) for s, rp in items]
         self.stream = torch.cuda.current_stream(dev)
         self.plan = Plan(descs, device=local, stream=self.stream)
@@ -271,7 +271,7 @@ class Runner:
             if R_dev is not None and len(items) == 1:
                 self.plan.load_R(i, R_dev)
             else:
-                for w0, blk in reflection_band_chunks(s, dev, chunk=16):
+                for w0, blk in reflection_band_chunks(s, dev, chunk=16 if s.n <= 2048 else 4):
                     self.plan.load_R(i, blk.contiguous(), w_begin=w0)
             td = S.survey_td(s)
             Gd = S.gd_traces(s, td, np.float32)
@@ -313,6 +313,7 @@ class Runner:
 
     def close(self):
         self.plan.close()
+        self.inputs = []
 
 
 def summarize(s, F, rprec, ms, steps, st, world=1):
@@ -414,15 +415,38 @@ def main_ours(args):
         del R_dev
         torch.cuda.empty_cache()
         bs = S.batching_surveys()
-        br = Runner([(x, "c64" if i % 2 == 0 else "split3") for i, x in enumerate(bs)], dev, local)
+        items = [(x, "c64" if i % 2 == 0 else "split3") for i, x in enumerate(bs)]
+        br = Runner(items, dev, local)
         bms, bst, _ = br.timed(5, 2)
         br.close()
         variants.append({"workload": "batching: 12 surveys, n 201-1201, nt 1024-4096, 1-256 focal points, "
-                                     "even surveys c64, odd surveys split3, one plan", "nfocal": br.F,
+                                     "even surveys c64, odd surveys split3, one plan, stream launches", "nfocal": br.F,
                          "value": br.F * 5 / (bms / 1e3), "ms_per_step": bms / 5,
                          "contract_ms_total": bst["contract_ms"] / 5, "epilogue_ms_total": bst["epilogue_ms"] / 5,
                          "gpu_launches_per_step": bst["launches"] / 5})
-        by = {(v["nfocal"], v["rprec"]): v["value"] for v in variants if "rprec" in v}
+        gr = Runner(items, dev, local, timing=False, graph=True)
+        gms, gst, _ = gr.timed(5, 2)
+        gr.close()
+        variants.append({"workload": "batching, same plan as above with each iteration replayed as one CUDA graph "
+                                     "(12 surveys on parallel branches)", "nfocal": gr.F,
+                         "value": gr.F * 5 / (gms / 1e3), "ms_per_step": gms / 5,
+                         "gpu_launches_per_step": gst["launches"] / 5})
+        # large survey: 4001 x 4001, nt = 4096, 984 bins; one focal batch of 64 of the 4001-point line
+        for lp in ("split3", "c64"):
+            ls = S.large_survey(nfocal=64)
+            lr = Runner([(ls, lp)], dev, local)
+            lms, lst, _ = lr.timed(2, 1)
+            lr.close()
+            del lr
+            torch.cuda.empty_cache()
+            d = summarize(ls, 64, lp, lms, 2, lst)
+            d["roofline"].pop("traffic", None)
+            d.update({"workload": f"large: 4001x4001, dx=5 m, nt=4096, 984 bins, R resident as {lp}, "
+                                  "focal batch of 64 of the 4001-point line",
+                      "nfocal": 64, "rprec": lp, "steps": 2,
+                      "full_line_seconds": 4001 / d["value"]})
+            variants.append(d)
+        by = {(v["nfocal"], v["rprec"]): v["value"] for v in variants if "rprec" in v and "workload" not in v}
         for vf in (64, 601):
             for vp in ("split", "split3", "cbf16"):
                 if (vf, vp) in by and (vf, "c64") in by:

@@ -99,6 +99,10 @@ typedef enum {
 
 /* mk_desc.flags */
 #define MK_FLAG_TIMING (1u << 0) /* record CUDA events around every kernel   */
+#define MK_FLAG_GRAPH  (1u << 1) /* replay iterations as one captured CUDA graph
+                                    (all surveys' kernels on parallel branches);
+                                    used when every survey sets it and none
+                                    sets MK_FLAG_TIMING                     */
 
 /* One survey.  nsrc == nrec is required (coincident sources/receivers). */
 typedef struct {

@@ -18,6 +18,7 @@ MK_R_C64, MK_R_CBF16, MK_R_CF16, MK_R_SPLIT_BF16, MK_R_SPLIT3_BF16 = range(5)
 MK_F_N, MK_F_F1P, MK_F_F1M, MK_F_F2P, MK_F_PMIN, MK_F_G, MK_F_GMINUS, MK_F_GPLUS = (1 << i for i in range(8))
 MK_F_ALL = 0xFF
 MK_FLAG_TIMING = 1
+MK_FLAG_GRAPH = 2
 
 
 class MkDesc(ctypes.Structure):

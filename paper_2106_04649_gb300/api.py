@@ -130,6 +130,7 @@ class Plan:
         if getattr(self, "handle", 0):
             B.mk_destroy(self.handle)
             self.handle = 0
+            self.workspace = None  # return the device memory to torch's allocator
 
     def __del__(self):
         try:

@@ -53,6 +53,12 @@ struct mk_plan_s {
   mk_stats_t stats{};
   std::vector<TimedPair> events;  // created once, reused
   size_t next_event = 0;
+  bool graph = false;                       // MK_FLAG_GRAPH on every survey
+  cudaStream_t cap_stream = nullptr;        // capture stream and per-survey branches
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  cudaGraphExec_t graph_exec = nullptr;
 };
 
 namespace {
@@ -158,6 +164,7 @@ size_t layout(Survey& sv, char* base) {
   v.Epart = reinterpret_cast<double*>(take((size_t)(v.ncols + 1) * sizeof(double)));
   v.counter = reinterpret_cast<unsigned*>(take(sizeof(unsigned)));
   v.err = reinterpret_cast<int*>(take(sizeof(int)));
+  v.iter = reinterpret_cast<int*>(take(sizeof(int)));
   v.tw = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));
   sv.energy = reinterpret_cast<double*>(take((size_t)kMaxIterSlots * v.F * sizeof(double)));
   return off;
@@ -374,7 +381,7 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
   p->s.resize(ndesc);
   size_t off = 0;
   char* base = static_cast<char*>(workspace);
-  bool timing = true;
+  bool timing = true, graph = true;
   for (int i = 0; i < ndesc; ++i) {
     Survey& sv = p->s[i];
     sv.d = d[i];
@@ -383,8 +390,10 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
     off += sv.bytes;
     sv.loaded.assign(sv.dev.nw, 0);
     timing = timing && (d[i].flags & MK_FLAG_TIMING);
+    graph = graph && (d[i].flags & MK_FLAG_GRAPH);
   }
   p->timing = timing;
+  p->graph = graph;
   // Zero the workspace (padding of R and Nw must be zero), then the twiddles.
   if ((e = cudaMemsetAsync(workspace, 0, off, p->stream)) != cudaSuccess) {
     delete p;
@@ -508,8 +517,9 @@ mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const d
   }
   MK_CUDA(p, mk::launch_windows(v, tsrc, eps_s, p->stream));
   MK_CUDA(p, mk::launch_init(v, gsrc, p->stream, p->num_sms));
-  p->stats.launches += 2;
-  p->stats.other_launches += 2;
+  MK_CUDA(p, mk::launch_set_iter(v, 0, p->stream));
+  p->stats.launches += 3;
+  p->stats.other_launches += 3;
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   sv->ready = true;
   sv->iter = 0;
@@ -518,7 +528,76 @@ mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const d
   return MK_OK;
 }
 
-mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
+}  // extern "C"
+
+namespace {
+
+// One iteration of every survey: contraction then epilogue, survey after
+// survey on one stream (timed launches), or -- when captured into a graph --
+// each survey on its own branch.
+mk_status launch_iteration(mk_plan_t p, bool timed, cudaStream_t main, bool branches) {
+  for (size_t i = 0; i < p->s.size(); ++i) {
+    Survey& sv = p->s[i];
+    cudaStream_t st = main;
+    if (branches) {
+      st = p->side[i];
+      MK_CUDA(p, cudaStreamWaitEvent(st, p->fork_ev, 0));
+    }
+    TimedPair* tp = timed ? next_pair(p, 0) : nullptr;
+    if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
+    int nl = 0;
+    MK_CUDA(p, mk::launch_contract(sv.dev, sv.umma, st, p->num_sms, &nl));
+    if (tp) MK_CUDA(p, cudaEventRecord(tp->b, st));
+    tp = timed ? next_pair(p, 1) : nullptr;
+    if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
+    MK_CUDA(p, mk::launch_epilogue(sv.dev, sv.energy, kMaxIterSlots, st, p->num_sms));
+    if (tp) MK_CUDA(p, cudaEventRecord(tp->b, st));
+    if (branches) {
+      MK_CUDA(p, cudaEventRecord(p->join_ev[i], st));
+      MK_CUDA(p, cudaStreamWaitEvent(main, p->join_ev[i], 0));
+    }
+  }
+  return MK_OK;
+}
+
+// Captures one iteration of all surveys into a graph (once per plan): the
+// iteration index lives on the device, so every replay is identical.
+mk_status build_graph(mk_plan_t p) {
+  if (p->graph_exec) return MK_OK;
+  if (!p->cap_stream) {
+    MK_CUDA(p, cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    MK_CUDA(p, cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming));
+    p->side.resize(p->s.size());
+    p->join_ev.resize(p->s.size());
+    for (size_t i = 0; i < p->s.size(); ++i) {
+      MK_CUDA(p, cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking));
+      MK_CUDA(p, cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming));
+    }
+  }
+  MK_CUDA(p, cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+  mk_status st = MK_OK;
+  cudaError_t e = cudaEventRecord(p->fork_ev, p->cap_stream);
+  if (e == cudaSuccess) st = launch_iteration(p, false, p->cap_stream, true);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &g);
+  if (e != cudaSuccess || st != MK_OK || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st != MK_OK) return st;
+    return fail(p, MK_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&p->graph_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p->graph_exec = nullptr;
+    return fail(p, MK_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+  }
+  return MK_OK;
+}
+
+}  // namespace
+
+extern "C" mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
   if (!p) return fail(nullptr, MK_ERR_ARG, "null plan");
   p->err[0] = 0;
   mk_status st = ensure_device(p);
@@ -529,36 +608,40 @@ mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
     if (!p->s[i].ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", (int)i);
     Ftot += p->s[i].dev.F;
   }
+  const bool use_graph = p->graph && !p->timing && niter > 0;
+  if (use_graph && (st = build_graph(p)) != MK_OK) return st;
   for (int done = 0; done < niter;) {
     const int chunk = niter - done < kMaxIterSlots ? niter - done : kMaxIterSlots;
+    std::vector<int> start(p->s.size());
+    for (size_t i = 0; i < p->s.size(); ++i) start[i] = p->s[i].iter;
     for (int it = 0; it < chunk; ++it) {
-      for (auto& sv : p->s) {
-        TimedPair* tp = next_pair(p, 0);
-        if (tp) MK_CUDA(p, cudaEventRecord(tp->a, p->stream));
-        int nl = 0;
-        MK_CUDA(p, mk::launch_contract(sv.dev, sv.umma, p->stream, p->num_sms, &nl));
-        if (tp) MK_CUDA(p, cudaEventRecord(tp->b, p->stream));
-        p->stats.launches += nl;
-        p->stats.contract_launches += nl;
-        tp = next_pair(p, 1);
-        if (tp) MK_CUDA(p, cudaEventRecord(tp->a, p->stream));
-        MK_CUDA(p, mk::launch_epilogue(sv.dev, sv.iter & 1, sv.energy + (size_t)it * sv.dev.F, p->stream,
-                                       p->num_sms));
-        if (tp) MK_CUDA(p, cudaEventRecord(tp->b, p->stream));
-        p->stats.launches++;
-        p->stats.epilogue_launches++;
-        sv.iter++;
-        sv.n_in_field = false;
-        sv.derived_valid = sv.gm_valid = sv.gp_valid = false;
+      if (use_graph) {
+        MK_CUDA(p, cudaGraphLaunch(p->graph_exec, p->stream));
+      } else if ((st = launch_iteration(p, p->timing, p->stream, false)) != MK_OK) {
+        return st;
       }
     }
+    for (auto& sv : p->s) {
+      p->stats.launches += 2 * chunk;
+      p->stats.contract_launches += chunk;
+      p->stats.epilogue_launches += chunk;
+      sv.iter += chunk;
+      sv.n_in_field = false;
+      sv.derived_valid = sv.gm_valid = sv.gp_valid = false;
+    }
     if (energy) {
+      // iteration i of a survey left its energies in ring slot i % kMaxIterSlots
       int foff = 0;
-      for (auto& sv : p->s) {
+      for (size_t i = 0; i < p->s.size(); ++i) {
+        Survey& sv = p->s[i];
+        const int s0 = start[i] % kMaxIterSlots;
+        const int n1 = chunk < kMaxIterSlots - s0 ? chunk : kMaxIterSlots - s0;
+        const size_t fb = (size_t)sv.dev.F * sizeof(double);
         MK_CUDA(p, cudaMemcpy2DAsync(energy + (size_t)done * Ftot + foff, (size_t)Ftot * sizeof(double),
-                                     sv.energy, (size_t)sv.dev.F * sizeof(double),
-                                     (size_t)sv.dev.F * sizeof(double), chunk, cudaMemcpyDeviceToHost,
-                                     p->stream));
+                                     sv.energy + (size_t)s0 * sv.dev.F, fb, fb, n1, cudaMemcpyDeviceToHost, p->stream));
+        if (n1 < chunk)
+          MK_CUDA(p, cudaMemcpy2DAsync(energy + (size_t)(done + n1) * Ftot + foff, (size_t)Ftot * sizeof(double),
+                                       sv.energy, fb, fb, chunk - n1, cudaMemcpyDeviceToHost, p->stream));
         foff += sv.dev.F;
       }
       MK_CUDA(p, cudaStreamSynchronize(p->stream));
@@ -568,6 +651,8 @@ mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
   }
   return MK_OK;
 }
+
+extern "C" {
 
 mk_status mk_fetch_fields(mk_plan_t p, int32_t survey, uint32_t mask, float* out, size_t out_bytes,
                           int32_t dst_on_device) {
@@ -634,8 +719,9 @@ mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float*
     q += field;
   }
   MK_CUDA(p, mk::launch_spectrum(v, v.fN, p->stream, p->num_sms));
-  p->stats.launches++;
-  p->stats.other_launches++;
+  MK_CUDA(p, mk::launch_set_iter(v, iteration, p->stream));
+  p->stats.launches += 2;
+  p->stats.other_launches += 2;
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   sv->iter = iteration;
   sv->n_in_field = true;
@@ -697,6 +783,11 @@ mk_status mk_destroy(mk_plan_t p) {
     cudaEventDestroy(tp.b);
   }
   for (auto& sv : p->s) mk::umma_destroy(sv.umma);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  for (auto st : p->side) cudaStreamDestroy(st);
+  for (auto ev : p->join_ev) cudaEventDestroy(ev);
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
   return MK_OK;
 }

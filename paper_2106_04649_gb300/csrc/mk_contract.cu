@@ -8,7 +8,10 @@
 
 namespace mk {
 
-cudaError_t prepare_contract() { return prepare_gemv(); }
+cudaError_t prepare_contract() {
+  cudaError_t e = prepare_gemv();
+  return e != cudaSuccess ? e : umma_prepare();
+}
 
 cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms, int* nlaunch) {
   *nlaunch = 1;

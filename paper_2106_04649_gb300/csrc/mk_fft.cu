@@ -346,7 +346,7 @@ __device__ __forceinline__ void forward_band_stage(const SurveyDev& s, float2* x
 
 template <int NT>
 __global__ void __launch_bounds__(threads_for(NT), NT <= 2048 ? 2 : 1)
-epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot, int G) {
+epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   constexpr int THREADS = threads_for(NT);
   constexpr int PJ = NT / THREADS;  // samples per thread
   extern __shared__ float4 smem_raw[];
@@ -361,6 +361,11 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot, int G) {
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
   __syncthreads();
 
+  // the iteration index lives on the device (the last CTA advances it), so
+  // every iteration launches with identical arguments (graph replay)
+  const int iter = *s.iter;
+  const int odd = iter & 1;
+  double* energy_slot = ring + (int64_t)(iter % slots) * s.F;
   const int bt = 2 * G;  // traces per block
   const int nblocks = (s.ncols + bt - 1) / bt;
   const float inv = s.inv_nt;
@@ -457,7 +462,10 @@ epilogue_kernel(SurveyDev s, int odd, double* __restrict__ energy_slot, int G) {
       for (int k = 0; k < s.ns; ++k) acc += __ldcg(s.Epart + (int64_t)f * s.ns + k);
       energy_slot[f] = acc;
     }
-    if (threadIdx.x == 0) *s.counter = 0u;
+    if (threadIdx.x == 0) {
+      *s.counter = 0u;
+      *s.iter = iter + 1;
+    }
   }
 }
 
@@ -696,7 +704,7 @@ int epi_pairs(int nw, size_t* bytes) {
 }
 
 template <int NT>
-cudaError_t launch_epi_nt(const SurveyDev& s, int odd, double* slot, cudaStream_t st, int num_sms) {
+cudaError_t launch_epi_nt(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
   size_t bytes = 0;
   int G = epi_pairs<NT>(s.nw, &bytes);
   // few traces: smaller blocks so that every SM gets work
@@ -705,7 +713,7 @@ cudaError_t launch_epi_nt(const SurveyDev& s, int odd, double* slot, cudaStream_
   const int nblocks = (s.ncols + 2 * G - 1) / (2 * G);
   int grid = num_sms * 2;
   if (grid > nblocks) grid = nblocks;
-  epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, odd, slot, G);
+  epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, ring, slots, G);
   return cudaGetLastError();
 }
 
@@ -758,9 +766,15 @@ bool epilogue_fits(int nt, int nw) {
   return bytes <= (size_t)kEpiSmemMax;
 }
 
-cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
-                            int num_sms) {
-#define MK_CALL(N) launch_epi_nt<N>(s, odd, energy_slot, st, num_sms)
+__global__ void set_iter_kernel(int* it, int v) { *it = v; }
+
+cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st) {
+  set_iter_kernel<<<1, 1, 0, st>>>(s.iter, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
+#define MK_CALL(N) launch_epi_nt<N>(s, ring, slots, st, num_sms)
   MK_NT_SWITCH(s.nt, MK_CALL)
 #undef MK_CALL
 }

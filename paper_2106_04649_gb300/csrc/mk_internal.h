@@ -50,18 +50,21 @@ struct SurveyDev {
   unsigned* counter;  // last-block counter of the epilogue
   const float2* tw;   // [nt] e^{-2 pi i q / nt}
   int* err;           // device error word (bounded waits that ran out); may be null
+  int* iter;          // device iteration index (parity and energy slot; advanced by the epilogue)
 };
 
 // Kernel launchers (return the launch status; the caller checks it).
 struct UmmaMaps;  // tensor maps of the tcgen05 contraction (mk_umma.cu)
 UmmaMaps* umma_create(const SurveyDev& s);
+cudaError_t umma_prepare();
 void umma_destroy(UmmaMaps* mp);
 cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms);
 cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms, int* nlaunch);
 cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
                                int num_sms);
-cudaError_t launch_epilogue(const SurveyDev& s, int odd, double* energy_slot, cudaStream_t st,
-                            int num_sms);
+// Energies of iteration i go to ring[(i % slots) * F + f].
+cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
+cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);
 bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the per-CTA limit
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);
 cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms);  // band spectrum of a field

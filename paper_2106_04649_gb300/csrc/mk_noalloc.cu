@@ -129,7 +129,7 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   const size_t c_bytes = 256;
   const size_t tw_bytes = align256((size_t)v.nt * sizeof(float2));
   const size_t slot_bytes = align256((size_t)v.F * sizeof(double));
-  const size_t need = nw_bytes + s_bytes + l_bytes + e_bytes + c_bytes + tw_bytes + slot_bytes;
+  const size_t need = nw_bytes + s_bytes + l_bytes + e_bytes + c_bytes + tw_bytes + slot_bytes + 256;
   if (need > MK_NOALLOC_SCRATCH_BYTES) {
     char buf[256];
     snprintf(buf, sizeof buf,
@@ -161,6 +161,8 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   off += e_bytes;
   v.counter = reinterpret_cast<unsigned*>(base + off);
   off += c_bytes;
+  v.iter = reinterpret_cast<int*>(base + off);  // starts at 0 (cleared below)
+  off += 256;
   float2* tw = reinterpret_cast<float2*>(base + off);
   off += tw_bytes;
   double* slot = reinterpret_cast<double*>(base + off);
@@ -190,8 +192,8 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
     int nl = 0;
     if ((e = mk::launch_contract(v, nullptr, stream, num_sms, &nl)) != cudaSuccess)
       return set_err(MK_ERR_CUDA, "contraction launch", cudaGetErrorString(e));
-    double* es = energy ? energy + (size_t)it * v.F : slot;
-    if ((e = mk::launch_epilogue(v, it & 1, es, stream, num_sms)) != cudaSuccess)
+    if ((e = energy ? mk::launch_epilogue(v, energy, niter, stream, num_sms)
+                    : mk::launch_epilogue(v, slot, 1, stream, num_sms)) != cudaSuccess)
       return set_err(MK_ERR_CUDA, "epilogue launch", cudaGetErrorString(e));
   }
   // The iterations accumulate f1plus and f1min; N, f2p and pmin follow from

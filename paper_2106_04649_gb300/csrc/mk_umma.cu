@@ -373,13 +373,6 @@ cudaError_t launch_bn(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, i
   const int stages = stages_for<BN, NA, NB>();
   const int stage = NA * UM * UKB * 2 + NB * BN * UKB * 2;
   const size_t smem = (size_t)stages * stage + 1024;
-  static bool attr_done = false;  // set once per process (same value for every device)
-  if (!attr_done) {
-    cudaError_t e = cudaFuncSetAttribute(umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
   UmmaParams P;
   P.S = s.S;
   P.ns = s.ns;
@@ -396,6 +389,23 @@ cudaError_t launch_bn(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, i
   umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE><<<grid, kThreads, smem, st>>>(mp.a0, mp.a1, mp.a2, mp.b0, mp.b1, mp.b2, P,
                                                                     stages);
   return cudaGetLastError();
+}
+
+template <int BN, int NA, int NB, int FMT, bool PROMOTE>
+cudaError_t set_attr_bn() {
+  const int stage = NA * UM * UKB * 2 + NB * BN * UKB * 2;
+  const size_t smem = (size_t)stages_for<BN, NA, NB>() * stage + 1024;
+  return cudaFuncSetAttribute(umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int NA, int NB, int FMT, bool PROMOTE>
+cudaError_t set_attr_na() {
+  cudaError_t e;
+  if ((e = set_attr_bn<16, NA, NB, FMT, PROMOTE>()) != cudaSuccess) return e;
+  if ((e = set_attr_bn<32, NA, NB, FMT, PROMOTE>()) != cudaSuccess) return e;
+  if ((e = set_attr_bn<64, NA, NB, FMT, PROMOTE>()) != cudaSuccess) return e;
+  return set_attr_bn<128, NA, NB, FMT, PROMOTE>();
 }
 
 template <int NA, int NB, int FMT, bool PROMOTE>
@@ -437,6 +447,16 @@ bool encode_map(CUtensorMap* tm, const void* base, int kprime, int rows, int nw,
 }
 
 }  // namespace
+
+// Shared-memory attributes of every instantiation (once per device, before
+// any launch, so that launches can be captured into graphs).
+cudaError_t umma_prepare() {
+  cudaError_t e;
+  if ((e = set_attr_na<3, 3, 1, true>()) != cudaSuccess) return e;
+  if ((e = set_attr_na<2, 2, 1, true>()) != cudaSuccess) return e;
+  if ((e = set_attr_na<1, 2, 1, false>()) != cudaSuccess) return e;
+  return set_attr_na<1, 2, 0, false>();
+}
 
 int umma_bn(int F) {
   const int n = 2 * F;
