@@ -120,11 +120,13 @@ __device__ __forceinline__ void stockham_pass(float2* x, const float2* tw, int N
       const int k = j & (Ns - 1);
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q][r] = x[P(j + r * NB)];
+      if (Ns > 1) {  // the first pass (Ns = 1) has unit twiddles
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = tw[toff + (r - 1) * Ns + k];
-        if (INV) w.y = -w.y;
-        v[q][r] = cmul(v[q][r], w);
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[toff + (r - 1) * Ns + k];
+          if (INV) w.y = -w.y;
+          v[q][r] = cmul(v[q][r], w);
+        }
       }
       dftR<INV, R>(v[q]);
     }
