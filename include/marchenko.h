@@ -99,6 +99,11 @@ typedef enum {
 
 /* mk_desc.flags */
 #define MK_FLAG_TIMING (1u << 0) /* record CUDA events around every kernel   */
+#define MK_FLAG_STREAM_R (1u << 2) /* keep R in pinned host memory and stream it
+                                    every contraction (complex FP32 only; see
+                                    mk_attach_R_host); a plan holding such a
+                                    survey launches its iterations on streams
+                                    (MK_FLAG_GRAPH is not applied)          */
 #define MK_FLAG_GRAPH  (1u << 1) /* replay iterations as one captured CUDA graph
                                     (all surveys' kernels on parallel branches);
                                     used when every survey sets it and none
@@ -165,6 +170,38 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
  */
 mk_status mk_load_R(mk_plan_t plan, int32_t survey, const void* Rw, int32_t w_begin,
                     int32_t w_count, int32_t src_on_device);
+
+/*
+ * mk_load_R_time - load R from its time traces (Implementation section: the
+ * reflection data is Fourier transformed once, before the iterations).  Each
+ * trace R(k, r, t), t = 0 .. nt-1, is transformed with the forward DFT
+ * R_m(k, r) = sum_j R(k, r, j) e^{-2 pi i j m / nt} (unnormalised) for the
+ * band m < n_w and stored in the plan's storage precision, exactly as a
+ * mk_load_R of those spectra (FP32 transform, FP64 twiddles).
+ *   Rt: float [nsrc][nrec][nt] (source row k, receiver r, sample), on the
+ *       host (src_on_device = 0; page-locked memory is read in place,
+ *       pageable memory is staged nfocal source rows at a time) or on the
+ *       device (1).
+ * Loads every bin; replaces any earlier mk_load_R of this survey.
+ * Errors: MK_ERR_ARG (bad survey, null), MK_ERR_STATE (streamed survey),
+ *         MK_ERR_CUDA.
+ */
+mk_status mk_load_R_time(mk_plan_t plan, int32_t survey, const float* Rt, int32_t src_on_device);
+
+/*
+ * mk_attach_R_host - out-of-core R for a survey planned with MK_FLAG_STREAM_R
+ * (the paper streams batches of shots to the GPUs when R exceeds their
+ * memory, Algorithm 2; here frequency chunks are streamed every contraction
+ * from page-locked host memory, double-buffered so that the copy of one
+ * chunk overlaps the contraction of the previous one).
+ *   Rpad:  page-locked host memory, complex64 [n_w][nsrc][r_pad] with
+ *          r_pad = nrec rounded up to a multiple of 32 and the padding zero;
+ *          the caller keeps it alive and unchanged until mk_destroy.
+ *   bytes: n_w * nsrc * r_pad * 8.
+ * Replaces mk_load_R for such surveys (mk_load_R returns MK_ERR_STATE).
+ * Errors: MK_ERR_ARG (size, not pinned), MK_ERR_STATE, MK_ERR_CUDA.
+ */
+mk_status mk_attach_R_host(mk_plan_t plan, int32_t survey, const void* Rpad, size_t bytes);
 
 /*
  * mk_set_Gd_window - start the Neumann series of one survey (Theory:

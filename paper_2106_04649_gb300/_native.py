@@ -19,6 +19,7 @@ MK_F_N, MK_F_F1P, MK_F_F1M, MK_F_F2P, MK_F_PMIN, MK_F_G, MK_F_GMINUS, MK_F_GPLUS
 MK_F_ALL = 0xFF
 MK_FLAG_TIMING = 1
 MK_FLAG_GRAPH = 2
+MK_FLAG_STREAM_R = 4
 
 
 class MkDesc(ctypes.Structure):
@@ -63,6 +64,8 @@ _SIGS = {
     "mk_destroy": (ctypes.c_int, [_P]),
     "mk_last_error": (ctypes.c_char_p, [_P]),
     "mk_image": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "mk_attach_R_host": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
+    "mk_load_R_time": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,
                                       _P]),
 }

@@ -70,6 +70,27 @@ class Plan:
             a, p = _ptr_host(Rw, np.complex64)
             B.mk_load_R(self.handle, survey, p, w_begin, a.shape[0], False)
 
+    def load_R_time(self, survey: int, Rt) -> None:
+        """R as time traces float32 [nsrc][nrec][nt] (device tensor or host array)."""
+        if isinstance(Rt, torch.Tensor) and Rt.is_cuda:
+            assert Rt.dtype == torch.float32 and Rt.is_contiguous()
+            B.mk_load_R_time(self.handle, survey, Rt.data_ptr(), True)
+        elif isinstance(Rt, torch.Tensor):
+            assert Rt.dtype == torch.float32 and Rt.is_contiguous()
+            B.mk_load_R_time(self.handle, survey, Rt.data_ptr(), False)
+        else:
+            a, p = _ptr_host(Rt, np.float32)
+            B.mk_load_R_time(self.handle, survey, p, False)
+
+    def attach_R_host(self, survey: int, Rpad) -> None:
+        """Out-of-core R (MK_FLAG_STREAM_R): a pinned torch CPU tensor, complex64
+        [n_w][nsrc][r_pad] (padding zero), kept alive by this plan."""
+        assert isinstance(Rpad, torch.Tensor) and Rpad.is_pinned() and Rpad.dtype == torch.complex64
+        assert Rpad.is_contiguous()
+        self._host_R = getattr(self, "_host_R", {})
+        self._host_R[survey] = Rpad
+        B.mk_attach_R_host(self.handle, survey, Rpad.data_ptr(), Rpad.numel() * 8)
+
     def set_Gd_window(self, survey: int, Gd, td, eps: float) -> None:
         """First arrivals G_d [F][n][nt] (float32) and t_d [F][n] (float64, s)."""
         if isinstance(Gd, torch.Tensor):

@@ -51,6 +51,14 @@ def mk_load_R(plan: int, survey: int, Rw: int, w_begin: int, w_count: int, src_o
     _check(N.load().mk_load_R(plan, survey, Rw, w_begin, w_count, int(src_on_device)), plan)
 
 
+def mk_load_R_time(plan: int, survey: int, Rt: int, src_on_device: bool) -> None:
+    _check(N.load().mk_load_R_time(plan, survey, Rt, 1 if src_on_device else 0), plan)
+
+
+def mk_attach_R_host(plan: int, survey: int, Rpad: int, nbytes: int) -> None:
+    _check(N.load().mk_attach_R_host(plan, survey, Rpad, nbytes), plan)
+
+
 def mk_set_Gd_window(plan: int, survey: int, Gd: int, td: int, eps_s: float, src_on_device: bool) -> None:
     _check(N.load().mk_set_Gd_window(plan, survey, Gd, td, eps_s, int(src_on_device)), plan)
 

@@ -34,6 +34,13 @@ struct Survey {
   bool derived_valid = false;  // f2p and pmin formed since the last change
   bool gm_valid = false, gp_valid = false;  // G^- and G^+ formed since the last change
   size_t offset = 0, bytes = 0;  // carving inside the workspace
+  // streaming of R from pinned host memory (MK_FLAG_STREAM_R)
+  bool stream_r = false;
+  int chunk_w = 0;                  // frequencies per streamed chunk
+  float2* rbuf[2] = {nullptr, nullptr};  // device chunk buffers
+  const float2* host_r = nullptr;   // caller's pinned R, [nw][ns][r_pad]
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ready_ev[2] = {nullptr, nullptr}, free_ev[2] = {nullptr, nullptr};
 };
 
 struct TimedPair {
@@ -104,6 +111,8 @@ mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
                 d.nt, band_bins(d));
   if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT3_BF16)
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: unknown R storage precision %d", i, d.rprec);
+  if ((d.flags & MK_FLAG_STREAM_R) && d.rprec != MK_R_C64)
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: streaming R from the host needs complex FP32 R", i);
   if ((int64_t)d.nsrc * d.nfocal > (int64_t)1 << 30)
     return fail(p, MK_ERR_ARG, "survey %d: nsrc * nfocal too large", i);
   return MK_OK;
@@ -132,7 +141,22 @@ size_t layout(Survey& sv, char* base) {
     return ptr;
   };
   const size_t field = (size_t)v.F * v.ns * v.nt * sizeof(float);
-  if (d.rprec == MK_R_C64) {
+  if (d.rprec == MK_R_C64 && (d.flags & MK_FLAG_STREAM_R)) {
+    // two chunk buffers of chunk_w frequencies: at least 4 chunks, at most 128 MB each
+    const size_t row = (size_t)v.ns * v.r_pad * sizeof(float2);
+    int cw = (v.nw + 3) / 4;
+    const int cap = (int)((size_t)128 << 20) / (int)(row ? row : 1);
+    if (cw > cap) cw = cap;
+    if (cw < 1) cw = 1;
+    sv.stream_r = true;
+    sv.chunk_w = cw;
+    sv.rbuf[0] = reinterpret_cast<float2*>(take((size_t)cw * row));
+    sv.rbuf[1] = reinterpret_cast<float2*>(take((size_t)cw * row));
+    v.R = nullptr;
+    v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
+    v.Rq0 = v.Rq1 = v.Rq2 = nullptr;
+    v.Bq0 = v.Bq1 = v.Bq2 = nullptr;
+  } else if (d.rprec == MK_R_C64) {
     v.R = reinterpret_cast<const float2*>(take((size_t)v.nw * v.ns * v.r_pad * sizeof(float2)));
     v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
     v.Rq0 = v.Rq1 = v.Rq2 = nullptr;
@@ -246,13 +270,48 @@ TimedPair* next_pair(mk_plan_t p, int kind) {
 //   f2p = f1plus - f1min(-t),  pmin = synthesis(f2p - N_last).
 // The pmin synthesis reuses the contraction; the band spectrum of N_last is
 // restored afterwards so the series continues unchanged.
+// The contraction of one survey on stream st.  With R streamed from pinned
+// host memory, R arrives in chunks of chunk_w frequencies on the survey's
+// copy stream, double-buffered: the copy of chunk c + 1 overlaps the
+// contraction of chunk c (each chunk is an independent set of frequencies).
+mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch) {
+  if (!sv.stream_r) {
+    MK_CUDA(p, mk::launch_contract(sv.dev, sv.umma, st, p->num_sms, nlaunch));
+    return MK_OK;
+  }
+  mk::SurveyDev v = sv.dev;
+  const size_t row = (size_t)v.ns * v.r_pad;  // complex elements per frequency
+  *nlaunch = 0;
+  int c = 0;
+  for (int w0 = 0; w0 < sv.dev.nw; w0 += sv.chunk_w, ++c) {
+    const int cw = sv.dev.nw - w0 < sv.chunk_w ? sv.dev.nw - w0 : sv.chunk_w;
+    const int b = c & 1;
+    // the buffer is free once the contraction that last read it is done
+    MK_CUDA(p, cudaStreamWaitEvent(sv.copy_stream, sv.free_ev[b], 0));
+    MK_CUDA(p, cudaMemcpyAsync(sv.rbuf[b], sv.host_r + (size_t)w0 * row, (size_t)cw * row * sizeof(float2),
+                               cudaMemcpyHostToDevice, sv.copy_stream));
+    MK_CUDA(p, cudaEventRecord(sv.ready_ev[b], sv.copy_stream));
+    MK_CUDA(p, cudaStreamWaitEvent(st, sv.ready_ev[b], 0));
+    v.R = sv.rbuf[b];
+    v.nw = cw;
+    v.Nw = sv.dev.Nw + (size_t)w0 * v.nw_stride;
+    v.S = sv.dev.S + (size_t)w0 * v.s_stride;
+    int nl = 0;
+    MK_CUDA(p, mk::launch_contract(v, nullptr, st, p->num_sms, &nl));
+    MK_CUDA(p, cudaEventRecord(sv.free_ev[b], st));
+    *nlaunch += nl;
+  }
+  return MK_OK;
+}
+
 // One plain synthesis (Eq. 1 before the mute) of a field into dst: band
 // spectrum, contraction, inverse transform.  Overwrites Nw and S.
 mk_status synthesize(mk_plan_t p, Survey& sv, const float* src, float* dst) {
   mk::SurveyDev& v = sv.dev;
   int nl = 0;
   MK_CUDA(p, mk::launch_spectrum(v, src, p->stream, p->num_sms));
-  MK_CUDA(p, mk::launch_contract(v, sv.umma, p->stream, p->num_sms, &nl));
+  mk_status st = contract(p, sv, p->stream, &nl);
+  if (st != MK_OK) return st;
   MK_CUDA(p, mk::launch_inverse(v, dst, 1, p->stream, p->num_sms));
   p->stats.launches += 2 + nl;
   p->stats.other_launches += 2 + nl;
@@ -313,7 +372,8 @@ mk_status materialize(mk_plan_t p, Survey& sv, uint32_t mask) {
   } else {
     int nl = 0;
     MK_CUDA(p, mk::launch_spectrum(v, v.scratch, p->stream, p->num_sms));
-    MK_CUDA(p, mk::launch_contract(v, sv.umma, p->stream, p->num_sms, &nl));
+    mk_status st = contract(p, sv, p->stream, &nl);
+    if (st != MK_OK) return st;
     MK_CUDA(p, mk::launch_inverse(v, v.pmin, 1, p->stream, p->num_sms));
     MK_CUDA(p, mk::launch_spectrum(v, v.fN, p->stream, p->num_sms));  // restore the spectrum of N_last
     p->stats.launches += 3 + nl;
@@ -432,6 +492,7 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
   p->err[0] = 0;
   if ((st = ensure_device(p)) != MK_OK) return st;
   const mk::SurveyDev& v = sv->dev;
+  if (sv->stream_r) return fail(p, MK_ERR_STATE, "survey %d streams R from the host: use mk_attach_R_host", survey);
   if (!Rw) return fail(p, MK_ERR_ARG, "null R pointer");
   if (w_begin < 0 || w_count < 0 || w_begin + w_count > v.nw)
     return fail(p, MK_ERR_ARG, "bins [%d, %d) outside the band [0, %d)", w_begin, w_begin + w_count, v.nw);
@@ -492,6 +553,93 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
   return MK_OK;
 }
 
+mk_status mk_load_R_time(mk_plan_t p, int32_t survey, const float* Rt, int32_t src_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  const mk::SurveyDev& v = sv->dev;
+  if (sv->stream_r) return fail(p, MK_ERR_STATE, "survey %d streams R from the host: use mk_attach_R_host", survey);
+  if (!Rt) return fail(p, MK_ERR_ARG, "null R pointer");
+  const float* src = Rt;
+  bool direct = src_on_device != 0;
+  if (!direct) {
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, Rt);
+    if (e == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer) {
+      src = static_cast<const float*>(attr.devicePointer);  // pinned: read in place
+      direct = true;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  // A view of R as a band-spectrum target: trace t = k * ns + r (source row
+  // k, receiver r) lands at bin m in row k, column r of R_m.
+  mk::SurveyDev t = v;
+  t.nw_stride = (int64_t)v.ns * v.r_pad;
+  t.rprec = v.rprec == MK_R_C64 ? 0 : 8 + v.rprec;
+  const int64_t row_floats = (int64_t)v.ns * v.nt;  // one source row of traces
+  // pageable host memory goes through the scratch field, F source rows at a time
+  const int64_t kb = direct ? v.ns : (int64_t)v.F;
+  for (int64_t k0 = 0; k0 < v.ns; k0 += kb) {
+    const int64_t n = v.ns - k0 < kb ? v.ns - k0 : kb;
+    const float* blk = src + k0 * row_floats;
+    if (!direct) {
+      MK_CUDA(p, cudaMemcpyAsync(v.scratch, Rt + k0 * row_floats, (size_t)(n * row_floats) * sizeof(float),
+                                 cudaMemcpyHostToDevice, p->stream));
+      blk = v.scratch;
+    }
+    t.F = (int)n;
+    t.ncols = (int)(n * v.ns);
+    const int64_t off = k0 * v.r_pad;  // complex elements
+    if (v.rprec == MK_R_C64) {
+      t.Nw = const_cast<float2*>(v.R) + off;
+    } else {
+      t.Rq0 = static_cast<const uint32_t*>(v.Rq0) + off;
+      t.Rq1 = v.Rq1 ? static_cast<const uint32_t*>(v.Rq1) + off : nullptr;
+      t.Rq2 = v.Rq2 ? static_cast<const uint32_t*>(v.Rq2) + off : nullptr;
+    }
+    MK_CUDA(p, mk::launch_spectrum(t, blk, p->stream, p->num_sms));
+    p->stats.launches++;
+    p->stats.other_launches++;
+  }
+  if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  for (int m = 0; m < v.nw; ++m) sv->loaded[m] = 1;
+  sv->nloaded = v.nw;
+  return MK_OK;
+}
+
+mk_status mk_attach_R_host(mk_plan_t p, int32_t survey, const void* Rpad, size_t bytes) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!sv->stream_r) return fail(p, MK_ERR_STATE, "survey %d keeps R resident: use mk_load_R", survey);
+  const mk::SurveyDev& v = sv->dev;
+  const size_t need = (size_t)v.nw * v.ns * v.r_pad * sizeof(float2);
+  if (!Rpad || bytes != need) return fail(p, MK_ERR_ARG, "host R must be %zu bytes ([n_w][nsrc][r_pad])", need);
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, Rpad);
+  if (e != cudaSuccess || attr.type != cudaMemoryTypeHost) {
+    cudaGetLastError();
+    return fail(p, MK_ERR_ARG, "host R must be page-locked (pinned) memory");
+  }
+  if (!sv->copy_stream) {
+    MK_CUDA(p, cudaStreamCreateWithFlags(&sv->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      MK_CUDA(p, cudaEventCreateWithFlags(&sv->ready_ev[b], cudaEventDisableTiming));
+      MK_CUDA(p, cudaEventCreateWithFlags(&sv->free_ev[b], cudaEventDisableTiming));
+      MK_CUDA(p, cudaEventRecord(sv->free_ev[b], p->stream));  // both buffers start free
+    }
+  }
+  sv->host_r = static_cast<const float2*>(Rpad);
+  for (int m = 0; m < v.nw; ++m) sv->loaded[m] = 1;
+  sv->nloaded = v.nw;
+  return MK_OK;
+}
+
 mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const double* td, double eps_s,
                            int32_t src_on_device) {
   Survey* sv = nullptr;
@@ -546,7 +694,8 @@ mk_status launch_iteration(mk_plan_t p, bool timed, cudaStream_t main, bool bran
     TimedPair* tp = timed ? next_pair(p, 0) : nullptr;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
     int nl = 0;
-    MK_CUDA(p, mk::launch_contract(sv.dev, sv.umma, st, p->num_sms, &nl));
+    mk_status cs = contract(p, sv, st, &nl);
+    if (cs != MK_OK) return cs;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->b, st));
     tp = timed ? next_pair(p, 1) : nullptr;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
@@ -608,7 +757,9 @@ extern "C" mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
     if (!p->s[i].ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", (int)i);
     Ftot += p->s[i].dev.F;
   }
-  const bool use_graph = p->graph && !p->timing && niter > 0;
+  bool streaming = false;
+  for (auto& sv : p->s) streaming = streaming || sv.stream_r;
+  const bool use_graph = p->graph && !p->timing && !streaming && niter > 0;
   if (use_graph && (st = build_graph(p)) != MK_OK) return st;
   for (int done = 0; done < niter;) {
     const int chunk = niter - done < kMaxIterSlots ? niter - done : kMaxIterSlots;
@@ -782,7 +933,14 @@ mk_status mk_destroy(mk_plan_t p) {
     cudaEventDestroy(tp.a);
     cudaEventDestroy(tp.b);
   }
-  for (auto& sv : p->s) mk::umma_destroy(sv.umma);
+  for (auto& sv : p->s) {
+    mk::umma_destroy(sv.umma);
+    if (sv.copy_stream) cudaStreamDestroy(sv.copy_stream);
+    for (int b = 0; b < 2; ++b) {
+      if (sv.ready_ev[b]) cudaEventDestroy(sv.ready_ev[b]);
+      if (sv.free_ev[b]) cudaEventDestroy(sv.free_ev[b]);
+    }
+  }
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (auto st : p->side) cudaStreamDestroy(st);
   for (auto ev : p->join_ev) cudaEventDestroy(ev);

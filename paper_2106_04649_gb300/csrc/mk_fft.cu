@@ -33,6 +33,7 @@
 #include <cuda_fp16.h>
 
 #include "mk_internal.h"
+#include "mk_rstore.cuh"
 
 namespace mk {
 namespace {
@@ -258,6 +259,14 @@ __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x,
       if (hasb) {
         const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
         row[(int64_t)fb * s.r_pad + kb] = B;
+      }
+    } else if (s.rprec >= 8) {
+      // time-domain R load: trace t = k * ns + r into the 16-bit R layout
+      const int fa = t0 / s.ns, ka = t0 - fa * s.ns;
+      store_r16(s, s.rprec - 8, (int64_t)m * s.nw_stride + (int64_t)fa * s.r_pad + ka, A);
+      if (hasb) {
+        const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
+        store_r16(s, s.rprec - 8, (int64_t)m * s.nw_stride + (int64_t)fb * s.r_pad + kb, B);
       }
     } else if (s.rprec == 2) {
       store_embedding<false>(s, m, t0, A.x, A.y);

@@ -7,18 +7,14 @@
 // copy.  (Implementation section: the reflection data is read, transformed
 // and kept for all iterations; here it stays resident in HBM.)
 
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
 #include "mk_internal.h"
+#include "mk_rstore.cuh"
 
 namespace mk {
 namespace {
 
-// Rows of complex FP32 into the 16-bit storage of the tensor-core path:
-// BF16 or FP16 rounding to nearest even (rprec 1, 2), BF16 hi + lo with
-// lo = rn(x - hi) (rprec 3), or BF16 hi + mid + lo with mid = rn(x - hi),
-// lo = rn(x - hi - mid) (rprec 4).  Output rows have 2 r_pad 16-bit values.
+// Rows of complex FP32 into the 16-bit storage of the tensor-core path
+// (conversion rules in store_r16).  Output rows have 2 r_pad 16-bit values.
 __global__ void __launch_bounds__(256) load_rows_q_kernel(const float2* __restrict__ src, SurveyDev s,
                                                          int64_t row0, int64_t rows) {
   const int lane = threadIdx.x & 31;
@@ -28,27 +24,7 @@ __global__ void __launch_bounds__(256) load_rows_q_kernel(const float2* __restri
   for (int64_t row = warp; row < rows; row += nwarps) {
     const float2* sr = src + row * nrec;
     const int64_t o = (row0 + row) * s.r_pad;  // in complex elements
-    for (int i = lane; i < nrec; i += 32) {
-      const float2 v = __ldg(sr + i);
-      if (s.rprec == 2) {
-        __half2 h = __floats2half2_rn(v.x, v.y);
-        reinterpret_cast<__half2*>(const_cast<void*>(s.Rq0))[o + i] = h;
-      } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
-        reinterpret_cast<__nv_bfloat162*>(const_cast<void*>(s.Rq0))[o + i] = h;
-        if (s.rprec >= 3) {
-          const float2 hf = __bfloat1622float2(h);
-          const float rx = v.x - hf.x, ry = v.y - hf.y;  // exact in FP32
-          const __nv_bfloat162 m2 = __floats2bfloat162_rn(rx, ry);
-          reinterpret_cast<__nv_bfloat162*>(const_cast<void*>(s.Rq1))[o + i] = m2;
-          if (s.rprec == 4) {
-            const float2 mf = __bfloat1622float2(m2);
-            reinterpret_cast<__nv_bfloat162*>(const_cast<void*>(s.Rq2))[o + i] =
-                __floats2bfloat162_rn(rx - mf.x, ry - mf.y);
-          }
-        }
-      }
-    }
+    for (int i = lane; i < nrec; i += 32) store_r16(s, s.rprec, o + i, __ldg(sr + i));
   }
 }
 

@@ -60,7 +60,8 @@ def test_workspace_size_and_validation_without_gpu():
     assert B.mk_workspace_size([d, d]) == 2 * n
     bad = [Desc(601, 600, 2048, 1, 0.004, 10.0), Desc(10, 10, 1000, 1, 0.004, 10.0),
            Desc(10, 10, 64, 0, 0.004, 10.0), Desc(10, 10, 64, 1, 0.0, 10.0),
-           Desc(10, 10, 64, 1, 0.004, 10.0, rprec=7)]
+           Desc(10, 10, 64, 1, 0.004, 10.0, rprec=7),
+           Desc(10, 10, 64, 1, 0.004, 10.0, rprec=4, flags=N.MK_FLAG_STREAM_R)]
     codes = []
     for b in bad:
         with pytest.raises(B.MarchenkoError) as ei:
@@ -68,7 +69,10 @@ def test_workspace_size_and_validation_without_gpu():
         codes.append(ei.value.status)
         assert B.mk_last_error(None)
     assert codes == [N.MK_ERR_UNSUPPORTED, N.MK_ERR_UNSUPPORTED, N.MK_ERR_ARG, N.MK_ERR_ARG,
-                     N.MK_ERR_UNSUPPORTED]
+                     N.MK_ERR_UNSUPPORTED, N.MK_ERR_UNSUPPORTED]
+    # streaming R keeps only two frequency chunks on the device
+    ds = Desc(601, 601, 2048, 1, 0.004, 10.0, 60.0, flags=N.MK_FLAG_STREAM_R)
+    assert B.mk_workspace_size([ds]) < n - r_bytes // 2
 
 
 def test_null_arguments_rejected_without_gpu():
