@@ -368,9 +368,14 @@ def main_ours(args):
         dist.barrier()
     head = summarize(s, F, args.rprec, ms, args.steps, st, world)
 
-    # end to end through the C ABI with host buffers (R, G_d, t_d in; energies and G out)
+    # end to end through the C ABI with host buffers (R, G_d, t_d in; energies and G out).
+    # Two plans on two streams alternate steps: while one plan runs step i, the
+    # other's copy of the R for step i + 1 (pinned host, asynchronous) is in
+    # flight, so the host link and the GPU work overlap.  Every step still
+    # copies its whole R, G_d and t_d in and its energies and G out.
     e2e = None
     if not args.no_e2e:
+        from paper_2106_04649_gb300.api import Desc, Plan
         Rh = R_dev.cpu().pin_memory()
         Gd_h, td_h = run.inputs[0][3], run.inputs[0][4]
         Gh = torch.from_numpy(Gd_h).pin_memory()
@@ -379,33 +384,41 @@ def main_ours(args):
         energy = torch.empty((NITER, F), dtype=torch.float64).pin_memory()
         h2d = Rh.numel() * 8 + Gd_h.nbytes + td_h.nbytes
         d2h = Gout.numel() * 4 + energy.numel() * 8
-        h = run.plan.handle
+        s2 = torch.cuda.Stream(dev)
+        other = Plan([Desc(s.n, s.n, s.nt, F, s.dt, s.dx, s.fmax_hz or 0.0, RPREC[args.rprec], 0)],
+                     device=local, stream=s2)
+        hs = [run.plan.handle, other.handle]
 
-        def e2e_step():
-            B.mk_load_R(h, 0, Rh.data_ptr(), 0, s.nw, False)
-            B.mk_set_Gd_window(h, 0, Gh.data_ptr(), th.data_ptr(), s.eps, False)
-            B.mk_iterate(h, NITER, energy.data_ptr())
-            B.mk_fetch_fields(h, 0, N.MK_F_G, Gout.data_ptr(), Gout.numel() * 4, False)
+        def e2e_steps(k):
+            B.mk_load_R(hs[0], 0, Rh.data_ptr(), 0, s.nw, N.MK_SRC_HOST_ASYNC)
+            for i in range(k):
+                x = hs[i % 2]
+                # returns once this plan's stream, its R copy included, is done
+                B.mk_set_Gd_window(x, 0, Gh.data_ptr(), th.data_ptr(), s.eps, False)
+                if i + 1 < k:  # the next step's R crosses the link while this step computes
+                    B.mk_load_R(hs[(i + 1) % 2], 0, Rh.data_ptr(), 0, s.nw, N.MK_SRC_HOST_ASYNC)
+                B.mk_iterate(x, NITER, energy.data_ptr())
+                B.mk_fetch_fields(x, 0, N.MK_F_G, Gout.data_ptr(), Gout.numel() * 4, False)
 
-        for _ in range(max(1, min(args.warmup, 3))):
-            e2e_step()
+        e2e_steps(max(2, min(args.warmup, 3)))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        ksteps = max(1, min(args.steps, 50))
+        ksteps = max(2, min(args.steps, 50))
         t0 = time.perf_counter()
-        for _ in range(ksteps):
-            e2e_step()
+        e2e_steps(ksteps)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         if world > 1:
             t = torch.tensor([el], dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             el = float(t.item())
+        other.close()
         e2e = {"value": world * F * ksteps / el, "unit": "focal points/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / ksteps, "steps": ksteps,
-               "path": "mk_load_R (pinned host, read in place by the load kernel) + mk_set_Gd_window (host) + "
-                       "mk_iterate(16, energies to host) + mk_fetch_fields(G to host)"}
+               "path": "per step: mk_load_R (pinned host R, asynchronous copy-engine transfer, issued one step "
+                       "ahead on a second plan) + mk_set_Gd_window (host) + mk_iterate(16, energies to host) + "
+                       "mk_fetch_fields(G to host); two plans alternate steps"}
     run.close()
 
     variants = []

@@ -47,7 +47,10 @@
  *    only during the call (the library copies from and to them);
  *  - all GPU work is issued on the stream given to mk_plan.  Calls that read
  *    host memory or write host outputs return after that work is complete;
- *    calls on device buffers only are asynchronous on the stream;
+ *    calls on device buffers only are asynchronous on the stream; mk_load_R
+ *    also takes page-locked host memory asynchronously (MK_SRC_HOST_ASYNC:
+ *    the caller keeps the buffer unchanged until the stream has passed the
+ *    copy, e.g. until the next call that returns host results);
  *  - a plan is not thread-safe: one host thread at a time per plan.
  *
  * Errors: every entry point returns mk_status and never aborts.  The message
@@ -99,6 +102,11 @@ typedef enum {
 
 /* mk_desc.flags */
 #define MK_FLAG_TIMING (1u << 0) /* record CUDA events around every kernel   */
+/* where a source buffer lives (the src_on_device argument) */
+#define MK_SRC_HOST 0       /* host memory; read before the call returns     */
+#define MK_SRC_DEVICE 1     /* device memory                                 */
+#define MK_SRC_HOST_ASYNC 2 /* page-locked host memory, read in stream order */
+
 #define MK_FLAG_STREAM_R (1u << 2) /* keep R in pinned host memory and stream it
                                     every contraction (complex FP32 only; see
                                     mk_attach_R_host); a plan holding such a
@@ -162,8 +170,11 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
  * one survey (Implementation section: the reflection data is read, Fourier
  * transformed and kept resident; here it is resident in HBM in the plan's
  * storage precision, rows padded for aligned loads).
- *   Rw: complex64 [w_count][nsrc][nrec] on the host (src_on_device = 0) or
- *       on the device (src_on_device = 1).
+ *   Rw: complex64 [w_count][nsrc][nrec] on the host (src_on_device =
+ *       MK_SRC_HOST), on the device (MK_SRC_DEVICE), or in page-locked host
+ *       memory read asynchronously in stream order (MK_SRC_HOST_ASYNC; the
+ *       call returns once the copy is queued, MK_ERR_ARG if the memory is
+ *       not page-locked).
  * Loading may be done in chunks of bins, in any order; mk_set_Gd_window
  * requires every bin 0 .. n_w-1 to have been loaded.
  * Errors: MK_ERR_ARG (bad survey index or bin range), MK_ERR_CUDA.

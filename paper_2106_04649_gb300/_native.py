@@ -20,6 +20,9 @@ MK_F_ALL = 0xFF
 MK_FLAG_TIMING = 1
 MK_FLAG_GRAPH = 2
 MK_FLAG_STREAM_R = 4
+MK_SRC_HOST = 0
+MK_SRC_DEVICE = 1
+MK_SRC_HOST_ASYNC = 2
 
 
 class MkDesc(ctypes.Structure):

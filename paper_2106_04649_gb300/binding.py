@@ -47,7 +47,8 @@ def mk_plan(descs, cuda_stream: int, workspace: int, workspace_bytes: int) -> in
     return int(out.value)
 
 
-def mk_load_R(plan: int, survey: int, Rw: int, w_begin: int, w_count: int, src_on_device: bool) -> None:
+def mk_load_R(plan: int, survey: int, Rw: int, w_begin: int, w_count: int, src_on_device: int) -> None:
+    """src_on_device: MK_SRC_HOST (0), MK_SRC_DEVICE (1) or MK_SRC_HOST_ASYNC (2)."""
     _check(N.load().mk_load_R(plan, survey, Rw, w_begin, w_count, int(src_on_device)), plan)
 
 

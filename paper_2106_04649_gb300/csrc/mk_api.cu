@@ -499,23 +499,34 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
   if (w_count == 0) return MK_OK;
   const int64_t rows = (int64_t)w_count * v.ns;
   const int64_t row0 = (int64_t)w_begin * v.ns;
+  if (src_on_device < MK_SRC_HOST || src_on_device > MK_SRC_HOST_ASYNC)
+    return fail(p, MK_ERR_ARG, "src_on_device must be MK_SRC_HOST, MK_SRC_DEVICE or MK_SRC_HOST_ASYNC");
   const float2* src = static_cast<const float2*>(Rw);
-  bool direct = src_on_device != 0;
+  bool direct = src_on_device == MK_SRC_DEVICE;
+  bool pinned = false;
   if (!direct) {
-    // pinned (page-locked) host memory is read by the kernel in place
+    // pinned (page-locked) host memory is read in place (mapped) by the
+    // conversion kernel or by the copy engine
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, Rw);
     if (e == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer) {
       src = static_cast<const float2*>(attr.devicePointer);
-      direct = true;
+      pinned = true;
     } else {
       cudaGetLastError();
     }
+    if (src_on_device == MK_SRC_HOST_ASYNC && !pinned)
+      return fail(p, MK_ERR_ARG, "MK_SRC_HOST_ASYNC needs page-locked host memory");
   }
+  // Page-locked host memory is read in place by the load kernel (one pass over
+  // the host link).  An asynchronous load runs beside other work, so it takes
+  // one block per SM, which already saturates the link, and leaves the rest
+  // of each SM to the kernels it overlaps.
+  const int max_blocks = src_on_device == MK_SRC_HOST_ASYNC ? p->num_sms : p->num_sms * 16;
   if (v.rprec == MK_R_C64) {
     float2* dst = const_cast<float2*>(v.R) + row0 * v.r_pad;
-    if (direct) {
-      MK_CUDA(p, mk::launch_load_rows(src, dst, rows, v.ns, v.r_pad, p->stream, p->num_sms));
+    if (direct || pinned) {
+      MK_CUDA(p, mk::launch_load_rows(src, dst, rows, v.ns, v.r_pad, p->stream, max_blocks));
       p->stats.launches++;
       p->stats.other_launches++;
     } else {
@@ -524,8 +535,8 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
                                    (size_t)v.ns * sizeof(float2), (size_t)rows, cudaMemcpyHostToDevice,
                                    p->stream));
     }
-  } else if (direct) {
-    MK_CUDA(p, mk::launch_load_rows_q(src, v, row0, rows, p->stream, p->num_sms));
+  } else if (direct || pinned) {
+    MK_CUDA(p, mk::launch_load_rows_q(src, v, row0, rows, p->stream, max_blocks));
     p->stats.launches++;
     p->stats.other_launches++;
   } else {
@@ -538,12 +549,12 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
       MK_CUDA(p, cudaMemcpyAsync(v.scratch, static_cast<const float2*>(Rw) + r * v.ns,
                                  (size_t)n * v.ns * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
       MK_CUDA(p, mk::launch_load_rows_q(reinterpret_cast<const float2*>(v.scratch), v, row0 + r, n, p->stream,
-                                        p->num_sms));
+                                        p->num_sms * 16));
       p->stats.launches++;
       p->stats.other_launches++;
     }
   }
-  if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  if (src_on_device == MK_SRC_HOST) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   for (int m = w_begin; m < w_begin + w_count; ++m) {
     if (!sv->loaded[m]) {
       sv->loaded[m] = 1;

@@ -214,8 +214,7 @@ __device__ __forceinline__ float round16(float a) {
 // embedding of the tensor-core contraction, split into hi + lo 16-bit parts:
 // rows 2f: (Nr, -Ni), 2f+1: (Ni, Nr) at columns 2k, 2k+1.
 template <bool BF16>
-__device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int t, float nr, float ni) {
-  const int f = t / s.ns, k = t - (t / s.ns) * s.ns;
+__device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int f, int k, float nr, float ni) {
   const int64_t kp = 2 * (int64_t)s.r_pad;
   const int64_t e0 = ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k;
   uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
@@ -268,12 +267,16 @@ __device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x,
         const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
         store_r16(s, s.rprec - 8, (int64_t)m * s.nw_stride + (int64_t)fb * s.r_pad + kb, B);
       }
-    } else if (s.rprec == 2) {
-      store_embedding<false>(s, m, t0, A.x, A.y);
-      if (hasb) store_embedding<false>(s, m, t0 + 1, B.x, B.y);
     } else {
-      store_embedding<true>(s, m, t0, A.x, A.y);
-      if (hasb) store_embedding<true>(s, m, t0 + 1, B.x, B.y);
+      const int fa = t0 / s.ns, ka = t0 - fa * s.ns;
+      const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
+      if (s.rprec == 2) {
+        store_embedding<false>(s, m, fa, ka, A.x, A.y);
+        if (hasb) store_embedding<false>(s, m, fb, kb, B.x, B.y);
+      } else {
+        store_embedding<true>(s, m, fa, ka, A.x, A.y);
+        if (hasb) store_embedding<true>(s, m, fb, kb, B.x, B.y);
+      }
     }
   }
 }
@@ -319,6 +322,27 @@ __device__ __forceinline__ void pack_pair(const SurveyDev& s, float2* x, int t0,
 
 __device__ __forceinline__ int stage_ld(int nw) { return nw | 1; }
 
+// Resident epilogue CTAs per SM the launch is built for (registers and
+// shared memory are sized to fit that many).
+__host__ __device__ constexpr int epi_ctas(int nt) { return nt <= 2048 ? 2 : 1; }
+__host__ __device__ constexpr size_t epi_smem_target(int nt) {
+  return epi_ctas(nt) >= 3 ? 73 * 1024 : 113 * 1024;
+}
+
+// The f1 window samples of a pair are prefetched into shared memory (2 NT
+// floats) up to NT = 4096; above that the shared memory is needed elsewhere.
+__host__ __device__ constexpr bool epi_prefetch(int nt) { return nt <= 4096; }
+__host__ __device__ constexpr size_t epi_base_bytes(int nt) {
+  return ((size_t)padded(nt) + nt) * sizeof(float2) + (epi_prefetch(nt) ? 2 * (size_t)nt * sizeof(float) : 0);
+}
+
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Dynamic shared memory the epilogue may use (below the 227 KB per-CTA limit,
 // leaving room for its static shared memory).
 constexpr int kEpiSmemMax = 220 * 1024;
@@ -356,16 +380,16 @@ __device__ __forceinline__ void forward_band_stage(const SurveyDev& s, float2* x
 }
 
 template <int NT>
-__global__ void __launch_bounds__(threads_for(NT), NT <= 2048 ? 2 : 1)
+__global__ void __launch_bounds__(threads_for(NT), epi_ctas(NT))
 epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   constexpr int THREADS = threads_for(NT);
-  constexpr int PJ = NT / THREADS;  // samples per thread
   extern __shared__ float4 smem_raw[];
-  float2* x = reinterpret_cast<float2*>(smem_raw);  // inverse transform
-  float2* y = x + padded(NT);                       // N_i pair for the forward transform
-  float2* tw = y + padded(NT);
+  float2* x = reinterpret_cast<float2*>(smem_raw);  // the pair: s, then N_i, then its transform
+  float2* tw = x + padded(NT);
   float2* stage = tw + NT;                          // [2G][ld] band spectra of the block
   const int ld = stage_ld(s.nw);
+  constexpr bool kPrefetch = epi_prefetch(NT);
+  float* hbuf = reinterpret_cast<float*>(stage + 2 * G * ld);  // [2][NT] f1 window samples (2G ld is even: 16-byte aligned)
   __shared__ double red[2 * (THREADS / 32)];
   __shared__ int s_last;
 
@@ -377,17 +401,29 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   const int iter = *s.iter;
   const int odd = iter & 1;
   double* energy_slot = ring + (int64_t)(iter % slots) * s.F;
-  const int bt = 2 * G;  // traces per block
+  const int bt = 2 * G;  // traces per block (2, 4 or 8)
   const int nblocks = (s.ncols + bt - 1) / bt;
+  const int cc = threadIdx.x & (bt - 1);                 // this thread's trace column
+  const int mc = threadIdx.x / bt, mstep = THREADS / bt;  // and its bins mc, mc + mstep, ...
   const float inv = s.inv_nt;
   float* __restrict__ f1 = odd ? s.f1p : s.f1m;
   for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
     const int tb = blk * bt;
     const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
-    // 1. the block's band spectra, one coalesced pass
-    for (int idx = threadIdx.x; idx < s.nw * ntr; idx += THREADS) {
-      const int m = idx / ntr, c = idx - (idx / ntr) * ntr;
-      stage[c * ld + m] = __ldg(s.S + (int64_t)m * s.s_stride + tb + c);
+    // 1. the block's band spectra, one coalesced pass (bt is a power of two
+    //    dividing THREADS, so each thread keeps one trace column c)
+    if (cc < ntr) {
+      const float2* src = s.S + tb + cc;
+      float2* dst = stage + cc * ld;
+      int m = mc;
+      for (; m + 7 * mstep < s.nw; m += 8 * mstep) {  // eight loads in flight per thread
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(src + (int64_t)(m + u * mstep) * s.s_stride);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) dst[m + u * mstep] = v[u];
+      }
+      for (; m < s.nw; m += mstep) dst[m] = __ldg(src + (int64_t)m * s.s_stride);
     }
     __syncthreads();
     for (int q = 0; 2 * q < ntr; ++q) {
@@ -395,46 +431,90 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       const bool hasb = 2 * q + 1 < ntr;
       float2* ra = stage + (2 * q) * ld;
       float2* rb = ra + ld;
-      // 2. Hermitian pack (bins outside the band are zero), inverse transform
-      pack_stage<NT, THREADS>(s, x, ra, rb, hasb);
-      __syncthreads();
-      fft_smem<NT, THREADS, true>(x, tw);
-      // 3. reverse, negate, mute; accumulate f1 (window samples only); N_i into y
       const int La = s.L[t0];
       const int Lb = hasb ? s.L[t0 + 1] : 0;
       const int64_t ba = field_offset(s, t0);
       const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
-      double ea = 0.0, eb = 0.0;
-      float ha[PJ], hb[PJ];
-#pragma unroll
-      for (int k = 0; k < PJ; ++k) {  // all loads first: one round trip
-        const int j = threadIdx.x + k * THREADS;
-        const int d = j < NT - j ? j : NT - j;
-        ha[k] = d < La ? f1[ba + j] : 0.f;
-        hb[k] = (hasb && d < Lb) ? f1[bb + j] : 0.f;
-      }
-#pragma unroll
-      for (int k = 0; k < PJ; ++k) {
-        const int j = threadIdx.x + k * THREADS;
-        const int d = j < NT - j ? j : NT - j;  // |signed index|
-        const float2 zj = x[P(j)];
-        const float2 zr = x[P((NT - j) & (NT - 1))];
-        const float sa = zj.x * inv, sb = zj.y * inv;
-        const float na = d < La ? -(zr.x * inv) : 0.f;
-        const float nb = d < Lb ? -(zr.y * inv) : 0.f;
-        y[P(j)] = make_float2(na, nb);
-        if (d < La) {
-          f1[ba + j] = ha[k] + (odd ? na : sa);  // odd: f1plus += N_i; even: f1min -= N_i(-t) = -theta s(t)
-          ea += (double)na * (double)na;
+      if constexpr (kPrefetch) {
+        // the window samples of f1 for this pair, copied asynchronously into
+        // shared memory while the inverse transform runs (16-byte chunks
+        // that touch the window |j| < L)
+        for (int c4 = threadIdx.x; c4 < NT / 2; c4 += THREADS) {
+          const int tr = c4 >= NT / 4;
+          const int j = 4 * (c4 - tr * (NT / 4));
+          const int L = tr ? Lb : La;
+          if (j < L || NT - (j + 3) < L) cp_async16(hbuf + tr * NT + j, f1 + (tr ? bb : ba) + j);
         }
-        if (d < Lb) {
-          f1[bb + j] = hb[k] + (odd ? nb : sb);
-          eb += (double)nb * (double)nb;
+        cp_async_commit();
+      }
+      // 2. Hermitian pack (bins outside the band are zero), inverse transform
+      pack_stage<NT, THREADS>(s, x, ra, rb, hasb);
+      __syncthreads();
+      fft_smem<NT, THREADS, true>(x, tw);
+      // 3. reverse, negate, mute; accumulate f1 (window samples only).  A
+      //    thread takes the mirror positions j and NT - j together (both have
+      //    |signed index| j and each one's N_i comes from the other's s), so
+      //    N_i overwrites s in place.
+      double ea = 0.0, eb = 0.0;
+      if constexpr (kPrefetch) {
+        cp_async_wait_all();
+        __syncthreads();
+      }
+      constexpr int PH = (NT / 2 + THREADS) / THREADS;  // mirror pairs j = 0 .. NT/2 per thread
+#pragma unroll
+      for (int k = 0; k < PH; ++k) {
+        const int j = threadIdx.x + k * THREADS;
+        if (j > NT / 2) continue;
+        const int jr = (NT - j) & (NT - 1);
+        const float2 zj = x[P(j)];
+        const float2 zr = x[P(jr)];
+        const bool ina = j < La, inb = j < Lb;
+        float haj = 0.f, har = 0.f, hbj = 0.f, hbr = 0.f;
+        if constexpr (kPrefetch) {
+          if (ina) {
+            haj = hbuf[j];
+            har = hbuf[jr];
+          }
+          if (inb) {
+            hbj = hbuf[NT + j];
+            hbr = hbuf[NT + jr];
+          }
+        } else {
+          if (ina) {
+            haj = f1[ba + j];
+            har = f1[ba + jr];
+          }
+          if (inb) {
+            hbj = f1[bb + j];
+            hbr = f1[bb + jr];
+          }
+        }
+        // N_i(j) = -theta s(-j) = -s(jr), N_i(jr) = -s(j) inside the window
+        const float naj = ina ? -(zr.x * inv) : 0.f, nar = ina ? -(zj.x * inv) : 0.f;
+        const float nbj = inb ? -(zr.y * inv) : 0.f, nbr = inb ? -(zj.y * inv) : 0.f;
+        x[P(j)] = make_float2(naj, nbj);
+        if (jr != j) x[P(jr)] = make_float2(nar, nbr);
+        // odd: f1plus += N_i; even: f1min -= N_i(-t) = theta s(t)
+        if (ina) {
+          f1[ba + j] = haj + (odd ? naj : -nar);
+          ea += (double)naj * (double)naj;
+          if (jr != j) {
+            f1[ba + jr] = har + (odd ? nar : -naj);
+            ea += (double)nar * (double)nar;
+          }
+        }
+        if (inb) {
+          f1[bb + j] = hbj + (odd ? nbj : -nbr);
+          eb += (double)nbj * (double)nbj;
+          if (jr != j) {
+            f1[bb + jr] = hbr + (odd ? nbr : -nbj);
+            eb += (double)nbr * (double)nbr;
+          }
         }
       }
       __syncthreads();
       // 4. forward transform of N_i, band spectra into the stage rows of this pair
-      forward_band_stage<NT, THREADS>(s, y, tw, ra, rb, hasb);
+      forward_band_stage<NT, THREADS>(s, x, tw, ra, rb, hasb);
       // 5. per-trace energies
       block_sum2<THREADS>(ea, eb, red);
       if (threadIdx.x == 0) {
@@ -444,34 +524,44 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       __syncthreads();
     }
     // 6. the block's new band spectra, one coalesced pass
-    for (int idx = threadIdx.x; idx < s.nw * ntr; idx += THREADS) {
-      const int m = idx / ntr, c = idx - (idx / ntr) * ntr;
-      const float2 v = stage[c * ld + m];
-      const int t = tb + c;
+    if (cc < ntr) {
+      const int t = tb + cc;
+      const int f = t / s.ns, k = t - f * s.ns;
       if (s.rprec == 0) {
-        const int f = t / s.ns, k = t - (t / s.ns) * s.ns;
-        s.Nw[(int64_t)m * s.nw_stride + (int64_t)f * s.r_pad + k] = v;
+        float2* dst = s.Nw + (int64_t)f * s.r_pad + k;
+        for (int m = mc; m < s.nw; m += mstep) dst[(int64_t)m * s.nw_stride] = stage[cc * ld + m];
       } else if (s.rprec == 2) {
-        store_embedding<false>(s, m, t, v.x, v.y);
+        for (int m = mc; m < s.nw; m += mstep) {
+          const float2 v = stage[cc * ld + m];
+          store_embedding<false>(s, m, f, k, v.x, v.y);
+        }
       } else {
-        store_embedding<true>(s, m, t, v.x, v.y);
+        for (int m = mc; m < s.nw; m += mstep) {
+          const float2 v = stage[cc * ld + m];
+          store_embedding<true>(s, m, f, k, v.x, v.y);
+        }
       }
     }
     __syncthreads();
   }
 
-  // The last CTA to finish sums the per-trace energies per focal point in a
-  // fixed order (k ascending), so the result does not depend on scheduling.
+  // The last CTA to finish sums the per-trace energies per focal point, one
+  // warp per focal point: lane l adds k = l, l + 32, ... in ascending order,
+  // then a fixed shuffle tree; the order never depends on scheduling.
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = (atomicAdd(s.counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (s_last) {
     __threadfence();
-    for (int f = threadIdx.x; f < s.F; f += THREADS) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int f = wid; f < s.F; f += THREADS / 32) {
+      const double* e = s.Epart + (int64_t)f * s.ns;
       double acc = 0.0;
-      for (int k = 0; k < s.ns; ++k) acc += __ldcg(s.Epart + (int64_t)f * s.ns + k);
-      energy_slot[f] = acc;
+      for (int k = lane; k < s.ns; k += 32) acc += __ldcg(e + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) energy_slot[f] = acc;
     }
     if (threadIdx.x == 0) {
       *s.counter = 0u;
@@ -702,14 +792,14 @@ cudaError_t launch_spec_nt(const SurveyDev& s, const float* src, cudaStream_t st
   return cudaGetLastError();
 }
 
-// Pairs per epilogue block: as many as keep two CTAs per SM (<= 113 KB of
-// shared memory each), at most 4, at least 1.
+// Pairs per epilogue block: as many as keep epi_ctas CTAs per SM within
+// shared memory: 4, 2 or 1.
 template <int NT>
 int epi_pairs(int nw, size_t* bytes) {
-  const size_t base = (2 * padded(NT) + NT) * sizeof(float2);
+  const size_t base = epi_base_bytes(NT);
   const size_t ld = (size_t)(nw | 1);
-  int G = 4;
-  while (G > 1 && base + 2 * G * ld * sizeof(float2) > 113 * 1024) --G;
+  int G = 4;  // a power of two: blocks of 2, 4 or 8 traces
+  while (G > 1 && base + 2 * G * ld * sizeof(float2) > epi_smem_target(NT)) G /= 2;
   *bytes = base + 2 * G * ld * sizeof(float2);
   return G;
 }
@@ -719,10 +809,10 @@ cudaError_t launch_epi_nt(const SurveyDev& s, double* ring, int slots, cudaStrea
   size_t bytes = 0;
   int G = epi_pairs<NT>(s.nw, &bytes);
   // few traces: smaller blocks so that every SM gets work
-  while (G > 1 && (s.ncols + 2 * G - 1) / (2 * G) < 2 * num_sms) --G;
-  bytes = (2 * padded(NT) + NT) * sizeof(float2) + 2 * (size_t)G * (size_t)(s.nw | 1) * sizeof(float2);
+  while (G > 1 && (s.ncols + 2 * G - 1) / (2 * G) < epi_ctas(NT) * num_sms) G /= 2;
+  bytes = epi_base_bytes(NT) + 2 * (size_t)G * (size_t)(s.nw | 1) * sizeof(float2);
   const int nblocks = (s.ncols + 2 * G - 1) / (2 * G);
-  int grid = num_sms * 2;
+  int grid = num_sms * epi_ctas(NT);
   if (grid > nblocks) grid = nblocks;
   epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, ring, slots, G);
   return cudaGetLastError();

@@ -60,8 +60,9 @@ cudaError_t umma_prepare();
 void umma_destroy(UmmaMaps* mp);
 cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms);
 cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms, int* nlaunch);
+// R row loads (grid-stride, at most max_blocks blocks of 256 threads)
 cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
-                               int num_sms);
+                               int max_blocks);
 // Energies of iteration i go to ring[(i % slots) * F + f].
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
 cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);
@@ -71,7 +72,7 @@ cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t s
 cudaError_t launch_inverse(const SurveyDev& s, float* dst, int mode, cudaStream_t st, int num_sms);
 cudaError_t launch_f2p(const SurveyDev& s, float* diff, cudaStream_t st, int num_sms);
 cudaError_t launch_load_rows(const float2* src, float2* dst, int64_t rows, int nrec, int r_pad, cudaStream_t st,
-                             int num_sms);
+                             int max_blocks);
 cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cudaStream_t st);
 cudaError_t launch_green(const SurveyDev& s, float* out, cudaStream_t st, int num_sms);
 cudaError_t launch_lincomb(const SurveyDev& s, float* out, const float* A, int revA, float alpha, const float* B,

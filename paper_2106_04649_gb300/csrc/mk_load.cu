@@ -44,18 +44,18 @@ __global__ void __launch_bounds__(256) load_rows_c64_kernel(const float2* __rest
 }  // namespace
 
 cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
-                               int num_sms) {
+                               int max_blocks) {
   int64_t grid = (rows + 7) / 8;
-  if (grid > (int64_t)num_sms * 16) grid = (int64_t)num_sms * 16;
+  if (grid > max_blocks) grid = max_blocks;
   if (grid < 1) grid = 1;
   load_rows_q_kernel<<<(unsigned)grid, 256, 0, st>>>(src, s, row0, rows);
   return cudaGetLastError();
 }
 
 cudaError_t launch_load_rows(const float2* src, float2* dst, int64_t rows, int nrec, int r_pad, cudaStream_t st,
-                             int num_sms) {
+                             int max_blocks) {
   int64_t grid = (rows + 7) / 8;
-  if (grid > (int64_t)num_sms * 16) grid = (int64_t)num_sms * 16;
+  if (grid > max_blocks) grid = max_blocks;
   if (grid < 1) grid = 1;
   load_rows_c64_kernel<<<(unsigned)grid, 256, 0, st>>>(src, dst, rows, nrec, r_pad);
   return cudaGetLastError();

@@ -173,24 +173,31 @@ def test_contraction_row_lengths(n):
 
 
 def test_load_paths_agree(tiny_inputs):
-    # pageable host, pinned host (read in place by the load kernel) in out-of-order
-    # chunks, and device sources must give bit-identical runs
+    # pageable host, pinned host in out-of-order chunks (synchronous and
+    # asynchronous in stream order), and device sources must give bit-identical runs
     import torch
+    from paper_2106_04649_gb300 import binding as B
+    from paper_2106_04649_gb300 import _native as N
     from paper_2106_04649_gb300.api import Plan
     s, R64, td, Gd64 = tiny_inputs
     R = R64.astype(np.complex64)
     Gd = Gd64.astype(np.float32)
     outs = []
-    for mode in ("pageable", "pinned", "device"):
+    for mode in ("pageable", "pinned", "pinned-async", "device"):
         p = Plan([desc_for(s)])
         if mode == "pageable":
             p.load_R(0, R)
-        elif mode == "pinned":
+        elif mode.startswith("pinned"):
             Rp = torch.from_numpy(R).pin_memory()
-            from paper_2106_04649_gb300 import binding as B
             nw, n = R.shape[0], R.shape[1]
+            how = N.MK_SRC_HOST_ASYNC if mode == "pinned-async" else N.MK_SRC_HOST
             for a, b in [(200, nw), (0, 77), (77, 200)]:
-                B.mk_load_R(p.handle, 0, Rp.data_ptr() + a * n * n * 8, a, b - a, False)
+                B.mk_load_R(p.handle, 0, Rp.data_ptr() + a * n * n * 8, a, b - a, how)
+            if how == N.MK_SRC_HOST_ASYNC:
+                # pageable memory cannot be read asynchronously
+                with pytest.raises(B.MarchenkoError) as ei:
+                    B.mk_load_R(p.handle, 0, R.ctypes.data, 0, 1, how)
+                assert ei.value.status == N.MK_ERR_ARG
         else:
             p.load_R(0, torch.from_numpy(R).cuda())
         p.set_Gd_window(0, Gd, td, s.eps)
