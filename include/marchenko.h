@@ -107,6 +107,10 @@ typedef enum {
 #define MK_SRC_DEVICE 1     /* device memory                                 */
 #define MK_SRC_HOST_ASYNC 2 /* page-locked host memory, read in stream order */
 
+#define MK_FLAG_AUTOTUNE (1u << 3) /* time the candidate tile shapes of the
+                                    survey's kernels at its first
+                                    mk_set_Gd_window and keep the fastest
+                                    (see mk_get_tuning)                     */
 #define MK_FLAG_STREAM_R (1u << 2) /* keep R in pinned host memory and stream it
                                     every contraction (complex FP32 only; see
                                     mk_attach_R_host); a plan holding such a
@@ -335,6 +339,32 @@ mk_status mk_get_stats(mk_plan_t plan, mk_stats_t* out, int32_t reset);
 #define MK_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float* Gd, const double* td, double eps_s,
                          int32_t niter, float* fields, double* energy, void* cuda_stream);
+
+/*
+ * Tuning of one survey's kernels (MK_FLAG_AUTOTUNE).  Candidates: the N tile
+ * of the tensor-core contraction (16, 32, 64 or 128 columns of the real
+ * field embedding, up to the first power of two covering 2 nfocal) and the
+ * pairs of traces per epilogue block (1, 2 or 4, within shared memory).  Each
+ * candidate runs once untimed and three times timed with CUDA events on the
+ * plan's stream, on the survey's own buffers, before the fields are
+ * initialised; the fastest is kept.  Choices are cached per process, keyed by
+ * (nsrc, nt, n_w, nfocal, rprec), so later plans of the same shape skip the
+ * timing.  Results do not depend on the choice.
+ */
+typedef struct {
+  int32_t tuned;        /* 0: heuristic choice, 1: timed now, 2: taken from the cache */
+  int32_t umma_bn;      /* N tile of the tensor-core contraction (0: not on that path) */
+  int32_t epi_pairs;    /* pairs per epilogue block (0: chosen at each launch) */
+  int32_t candidates;   /* candidates timed */
+  float contract_ms;    /* best contraction time seen while tuning (0 if none) */
+  float epilogue_ms;    /* best epilogue time seen while tuning (0 if none) */
+} mk_tuning_t;
+
+/*
+ * mk_get_tuning - the kernel choices of one survey (after mk_set_Gd_window
+ * when tuned).  Errors: MK_ERR_ARG (bad survey, null).
+ */
+mk_status mk_get_tuning(mk_plan_t plan, int32_t survey, mk_tuning_t* out);
 
 /* mk_destroy - release the plan's host state (not the caller's workspace).
  * Synchronises the plan's stream.  NULL is accepted. */

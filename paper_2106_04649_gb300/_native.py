@@ -20,6 +20,7 @@ MK_F_ALL = 0xFF
 MK_FLAG_TIMING = 1
 MK_FLAG_GRAPH = 2
 MK_FLAG_STREAM_R = 4
+MK_FLAG_AUTOTUNE = 8
 MK_SRC_HOST = 0
 MK_SRC_DEVICE = 1
 MK_SRC_HOST_ASYNC = 2
@@ -52,6 +53,17 @@ class MkStats(ctypes.Structure):
     ]
 
 
+class MkTuning(ctypes.Structure):
+    _fields_ = [
+        ("tuned", ctypes.c_int32),
+        ("umma_bn", ctypes.c_int32),
+        ("epi_pairs", ctypes.c_int32),
+        ("candidates", ctypes.c_int32),
+        ("contract_ms", ctypes.c_float),
+        ("epilogue_ms", ctypes.c_float),
+    ]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "mk_workspace_size": (ctypes.c_int, [ctypes.POINTER(MkDesc), ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
@@ -69,6 +81,7 @@ _SIGS = {
     "mk_image": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "mk_attach_R_host": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
     "mk_load_R_time": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
+    "mk_get_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(MkTuning)]),
     "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,
                                       _P]),
 }

@@ -144,6 +144,10 @@ class Plan:
             a, ptr = _ptr_host(fields, np.float32)
             B.mk_set_fields(self.handle, survey, mask, ptr, a.nbytes, iteration, False)
 
+    def tuning(self, survey: int) -> dict:
+        """Kernel shapes of a survey (timed at its first set_Gd_window with MK_FLAG_AUTOTUNE)."""
+        return B.mk_get_tuning(self.handle, survey)
+
     def stats(self, reset: bool = False) -> dict:
         return B.mk_get_stats(self.handle, reset)
 

@@ -52,6 +52,12 @@ def mk_load_R(plan: int, survey: int, Rw: int, w_begin: int, w_count: int, src_o
     _check(N.load().mk_load_R(plan, survey, Rw, w_begin, w_count, int(src_on_device)), plan)
 
 
+def mk_get_tuning(plan: int, survey: int) -> dict:
+    t = N.MkTuning()
+    _check(N.load().mk_get_tuning(plan, survey, ctypes.byref(t)), plan)
+    return {name: getattr(t, name) for name, _ in N.MkTuning._fields_}
+
+
 def mk_load_R_time(plan: int, survey: int, Rt: int, src_on_device: bool) -> None:
     _check(N.load().mk_load_R_time(plan, survey, Rt, 1 if src_on_device else 0), plan)
 

@@ -6,7 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/marchenko.h"
@@ -41,6 +44,7 @@ struct Survey {
   const float2* host_r = nullptr;   // caller's pinned R, [nw][ns][r_pad]
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ready_ev[2] = {nullptr, nullptr}, free_ev[2] = {nullptr, nullptr};
+  mk_tuning_t tuning = {0, 0, 0, 0, 0.f, 0.f};
 };
 
 struct TimedPair {
@@ -66,6 +70,7 @@ struct mk_plan_s {
   cudaEvent_t fork_ev = nullptr;
   std::vector<cudaEvent_t> join_ev;
   cudaGraphExec_t graph_exec = nullptr;
+  int* err_host = nullptr;  // page-locked copy of the device error words (one per survey)
 };
 
 namespace {
@@ -134,6 +139,7 @@ size_t layout(Survey& sv, char* base) {
   v.c = (float)(d.dx * d.dt);
   v.inv_nt = 1.0f / (float)d.nt;
   v.rprec = d.rprec;
+  v.epi_g = 0;
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
     char* ptr = base ? base + off : nullptr;
@@ -235,10 +241,15 @@ mk_status ensure_device(mk_plan_t p) {
 
 // Reads and clears the device error words (after a stream synchronisation).
 mk_status check_device_errors(mk_plan_t p) {
+  if (!p->err_host) {
+    // page-locked, so the read is an ordinary stream-ordered copy
+    MK_CUDA(p, cudaHostAlloc(reinterpret_cast<void**>(&p->err_host), p->s.size() * sizeof(int), cudaHostAllocDefault));
+  }
+  for (size_t i = 0; i < p->s.size(); ++i)
+    MK_CUDA(p, cudaMemcpyAsync(p->err_host + i, p->s[i].dev.err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  MK_CUDA(p, cudaStreamSynchronize(p->stream));
   for (size_t i = 0; i < p->s.size(); ++i) {
-    int h = 0;
-    MK_CUDA(p, cudaMemcpyAsync(&h, p->s[i].dev.err, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    MK_CUDA(p, cudaStreamSynchronize(p->stream));
+    const int h = p->err_host[i];
     if (h != 0) {
       MK_CUDA(p, cudaMemsetAsync(p->s[i].dev.err, 0, sizeof(int), p->stream));
       return fail(p, MK_ERR_TIMEOUT, "survey %d: a bounded device wait ran out (code %d); results are invalid",
@@ -301,6 +312,112 @@ mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch) {
     MK_CUDA(p, cudaEventRecord(sv.free_ev[b], st));
     *nlaunch += nl;
   }
+  return MK_OK;
+}
+
+// Tuning (MK_FLAG_AUTOTUNE): per-process cache of the fastest kernel shapes,
+// keyed by (nsrc, nt, n_w, nfocal, rprec).
+struct TuneChoice {
+  int bn, g;
+  float contract_ms, epilogue_ms;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, TuneChoice> g_tune_cache;
+
+// Times each candidate shape of the survey's contraction and epilogue on its
+// own buffers (the fields are initialised afterwards) and keeps the fastest.
+mk_status tune_survey(mk_plan_t p, Survey& sv) {
+  mk::SurveyDev& v = sv.dev;
+  const auto key = std::make_tuple(v.ns, v.nt, v.nw, v.F, v.rprec);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      if (sv.umma && !mk::umma_set_bn(sv.umma, v, it->second.bn))
+        return fail(p, MK_ERR_CUDA, "tensor map encoding for N tile %d failed", it->second.bn);
+      v.epi_g = it->second.g;
+      sv.tuning = {2, sv.umma ? it->second.bn : 0, it->second.g, 0, it->second.contract_ms, it->second.epilogue_ms};
+      return MK_OK;
+    }
+  }
+  cudaEvent_t e0, e1;
+  MK_CUDA(p, cudaEventCreate(&e0));
+  MK_CUDA(p, cudaEventCreate(&e1));
+  int candidates = 0;
+  mk_status result = MK_OK;
+  // best of three timed runs after one untimed run
+  auto time_it = [&](auto&& launch, float* best) -> mk_status {
+    *best = 1e30f;
+    for (int r = 0; r < 4; ++r) {
+      MK_CUDA(p, cudaEventRecord(e0, p->stream));
+      int nl = 0;
+      mk_status st = launch(&nl);
+      if (st != MK_OK) return st;
+      MK_CUDA(p, cudaEventRecord(e1, p->stream));
+      MK_CUDA(p, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      MK_CUDA(p, cudaEventElapsedTime(&ms, e0, e1));
+      if (r > 0 && ms < *best) *best = ms;
+    }
+    ++candidates;
+    return MK_OK;
+  };
+  TuneChoice best = {sv.umma ? mk::umma_get_bn(sv.umma) : 0, 0, 0.f, 0.f};
+  do {
+    if (sv.umma) {
+      int cover = 16;
+      while (cover < 2 * v.F && cover < 128) cover *= 2;
+      float best_ms = 1e30f;
+      for (int bn = 16; bn <= cover; bn *= 2) {
+        if (!mk::umma_set_bn(sv.umma, v, bn)) {
+          result = fail(p, MK_ERR_CUDA, "tensor map encoding for N tile %d failed", bn);
+          break;
+        }
+        float ms = 0.f;
+        result = time_it([&](int* nl) { return contract(p, sv, p->stream, nl); }, &ms);
+        if (result != MK_OK) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best.bn = bn;
+        }
+      }
+      if (result != MK_OK) break;
+      if (!mk::umma_set_bn(sv.umma, v, best.bn)) {
+        result = fail(p, MK_ERR_CUDA, "tensor map encoding for N tile %d failed", best.bn);
+        break;
+      }
+      best.contract_ms = best_ms;
+    }
+    // the epilogue advances the device iteration index: start it from 0
+    MK_CUDA(p, mk::launch_set_iter(v, 0, p->stream));
+    const int gmax = mk::epilogue_max_pairs(v.nt, v.nw);
+    float best_ms = 1e30f;
+    for (int g = 1; g <= gmax; g *= 2) {
+      v.epi_g = g;
+      float ms = 0.f;
+      result = time_it(
+          [&](int* nl) -> mk_status {
+            *nl = 1;
+            MK_CUDA(p, mk::launch_epilogue(v, sv.energy, kMaxIterSlots, p->stream, p->num_sms));
+            return MK_OK;
+          },
+          &ms);
+      if (result != MK_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.g = g;
+      }
+    }
+    if (result != MK_OK) break;
+    v.epi_g = best.g;
+    best.epilogue_ms = best_ms;
+  } while (false);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != MK_OK) return result;
+  sv.tuning = {1, sv.umma ? best.bn : 0, best.g, candidates, best.contract_ms, best.epilogue_ms};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
   return MK_OK;
 }
 
@@ -651,6 +768,19 @@ mk_status mk_attach_R_host(mk_plan_t p, int32_t survey, const void* Rpad, size_t
   return MK_OK;
 }
 
+mk_status mk_get_tuning(mk_plan_t p, int32_t survey, mk_tuning_t* out) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  if (!out) return fail(p, MK_ERR_ARG, "null output");
+  *out = sv->tuning;
+  if (!out->tuned) {
+    out->umma_bn = sv->umma ? mk::umma_get_bn(sv->umma) : 0;
+    out->epi_pairs = sv->dev.epi_g;
+  }
+  return MK_OK;
+}
+
 mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const double* td, double eps_s,
                            int32_t src_on_device) {
   Survey* sv = nullptr;
@@ -675,6 +805,14 @@ mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const d
     gsrc = v.scratch;
   }
   MK_CUDA(p, mk::launch_windows(v, tsrc, eps_s, p->stream));
+  if ((sv->d.flags & MK_FLAG_AUTOTUNE) && !sv->tuning.tuned) {
+    // before the fields are initialised: tuning runs write them
+    if ((st = tune_survey(p, *sv)) != MK_OK) return st;
+    if (p->graph_exec) {  // captured launches hold the old shapes
+      cudaGraphExecDestroy(p->graph_exec);
+      p->graph_exec = nullptr;
+    }
+  }
   MK_CUDA(p, mk::launch_init(v, gsrc, p->stream, p->num_sms));
   MK_CUDA(p, mk::launch_set_iter(v, 0, p->stream));
   p->stats.launches += 3;
@@ -957,6 +1095,7 @@ mk_status mk_destroy(mk_plan_t p) {
   for (auto ev : p->join_ev) cudaEventDestroy(ev);
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->err_host) cudaFreeHost(p->err_host);
   delete p;
   return MK_OK;
 }

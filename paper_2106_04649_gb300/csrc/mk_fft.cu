@@ -146,6 +146,68 @@ __device__ __forceinline__ void stockham_pass(float2* x, const float2* tw, int N
   __syncthreads();
 }
 
+// The same pass out of place: reads in, writes out, one barrier.  The pass
+// before wrote in and read out before its own barrier, so nothing else
+// orders the two.
+template <int NT, int THREADS, bool INV, int R>
+__device__ __forceinline__ void stockham_pass_pp(const float2* in, float2* out, const float2* tw, int Ns, int toff) {
+  constexpr int NB = NT / R;
+  constexpr int PB = (NB + THREADS - 1) / THREADS;
+#pragma unroll
+  for (int q = 0; q < PB; ++q) {
+    const int j = threadIdx.x + q * THREADS;
+    if (j < NB) {
+      const int k = j & (Ns - 1);
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = in[P(j + r * NB)];
+      if (Ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[toff + (r - 1) * Ns + k];
+          if (INV) w.y = -w.y;
+          v[r] = cmul(v[r], w);
+        }
+      }
+      dftR<INV, R>(v);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) out[P(base + r * Ns)] = v[r];
+    }
+  }
+  __syncthreads();
+}
+
+// Complex DFT of a[P(0 .. NT-1)] ping-ponging between a and b; returns the
+// buffer that holds the result (a for an even number of passes).
+template <int NT, int THREADS, bool INV>
+__device__ __forceinline__ float2* fft_smem_pp(float2* a, float2* b, const float2* tw) {
+  constexpr int LOG2 = ilog2(NT);
+  constexpr int N8 = LOG2 / 3;
+  constexpr int REM = LOG2 % 3;
+  int Ns = 1, toff = 0;
+  float2* in = a;
+  float2* out = b;
+#pragma unroll 1
+  for (int p = 0; p < N8; ++p) {
+    stockham_pass_pp<NT, THREADS, INV, 8>(in, out, tw, Ns, toff);
+    toff += 7 * Ns;
+    Ns *= 8;
+    float2* t = in;
+    in = out;
+    out = t;
+  }
+  if (REM == 1) {
+    stockham_pass_pp<NT, THREADS, INV, 2>(in, out, tw, Ns, toff);
+    in = out;
+  }
+  if (REM == 2) {
+    stockham_pass_pp<NT, THREADS, INV, 4>(in, out, tw, Ns, toff);
+    in = out;
+  }
+  return in;
+}
+
 // In-place complex DFT of x[P(0 .. NT-1)] (unnormalised; sign -1 forward,
 // +1 inverse): radix-8 passes, then one radix-2 or radix-4 pass when log2 NT
 // is not a multiple of 3.  The twiddle table holds the passes' tables back to
@@ -332,8 +394,12 @@ __host__ __device__ constexpr size_t epi_smem_target(int nt) {
 // The f1 window samples of a pair are prefetched into shared memory (2 NT
 // floats) up to NT = 4096; above that the shared memory is needed elsewhere.
 __host__ __device__ constexpr bool epi_prefetch(int nt) { return nt <= 4096; }
+// Up to NT = 4096 the transforms ping-pong between two buffers (one barrier
+// per pass instead of two).
+__host__ __device__ constexpr bool epi_pingpong(int nt) { return nt <= 4096; }
 __host__ __device__ constexpr size_t epi_base_bytes(int nt) {
-  return ((size_t)padded(nt) + nt) * sizeof(float2) + (epi_prefetch(nt) ? 2 * (size_t)nt * sizeof(float) : 0);
+  return ((epi_pingpong(nt) ? 2 : 1) * (size_t)padded(nt) + nt) * sizeof(float2) +
+         (epi_prefetch(nt) ? 2 * (size_t)nt * sizeof(float) : 0);
 }
 
 __device__ __forceinline__ void cp_async16(float* dst, const float* src) {
@@ -366,14 +432,13 @@ __device__ __forceinline__ void pack_stage(const SurveyDev& s, float2* x, const 
   }
 }
 
-// Forward transform of the pair in x (a + i b); band spectra into stage rows.
+// Band spectra of the transformed pair z (a + i b) into stage rows.
 template <int NT, int THREADS>
-__device__ __forceinline__ void forward_band_stage(const SurveyDev& s, float2* x, const float2* tw, float2* ra,
-                                                   float2* rb, bool hasb) {
-  fft_smem<NT, THREADS, false>(x, tw);
+__device__ __forceinline__ void unpack_band_stage(const SurveyDev& s, const float2* z, float2* ra, float2* rb,
+                                                  bool hasb) {
   for (int m = threadIdx.x; m < s.nw; m += THREADS) {
-    const float2 zm = x[P(m)];
-    const float2 zc = cconj(x[P((NT - m) & (NT - 1))]);
+    const float2 zm = z[P(m)];
+    const float2 zc = cconj(z[P((NT - m) & (NT - 1))]);
     ra[m] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
     if (hasb) rb[m] = make_float2(0.5f * (zm.y - zc.y), -0.5f * (zm.x - zc.x));
   }
@@ -384,8 +449,10 @@ __global__ void __launch_bounds__(threads_for(NT), epi_ctas(NT))
 epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   constexpr int THREADS = threads_for(NT);
   extern __shared__ float4 smem_raw[];
+  constexpr bool kPingPong = epi_pingpong(NT);
   float2* x = reinterpret_cast<float2*>(smem_raw);  // the pair: s, then N_i, then its transform
-  float2* tw = x + padded(NT);
+  float2* y = x + (kPingPong ? padded(NT) : 0);     // second buffer of the ping-pong transforms
+  float2* tw = y + padded(NT);
   float2* stage = tw + NT;                          // [2G][ld] band spectra of the block
   const int ld = stage_ld(s.nw);
   constexpr bool kPrefetch = epi_prefetch(NT);
@@ -450,7 +517,12 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       // 2. Hermitian pack (bins outside the band are zero), inverse transform
       pack_stage<NT, THREADS>(s, x, ra, rb, hasb);
       __syncthreads();
-      fft_smem<NT, THREADS, true>(x, tw);
+      float2* z = x;
+      if constexpr (kPingPong) {
+        z = fft_smem_pp<NT, THREADS, true>(x, y, tw);
+      } else {
+        fft_smem<NT, THREADS, true>(x, tw);
+      }
       // 3. reverse, negate, mute; accumulate f1 (window samples only).  A
       //    thread takes the mirror positions j and NT - j together (both have
       //    |signed index| j and each one's N_i comes from the other's s), so
@@ -466,8 +538,8 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
         const int j = threadIdx.x + k * THREADS;
         if (j > NT / 2) continue;
         const int jr = (NT - j) & (NT - 1);
-        const float2 zj = x[P(j)];
-        const float2 zr = x[P(jr)];
+        const float2 zj = z[P(j)];
+        const float2 zr = z[P(jr)];
         const bool ina = j < La, inb = j < Lb;
         float haj = 0.f, har = 0.f, hbj = 0.f, hbr = 0.f;
         if constexpr (kPrefetch) {
@@ -492,8 +564,8 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
         // N_i(j) = -theta s(-j) = -s(jr), N_i(jr) = -s(j) inside the window
         const float naj = ina ? -(zr.x * inv) : 0.f, nar = ina ? -(zj.x * inv) : 0.f;
         const float nbj = inb ? -(zr.y * inv) : 0.f, nbr = inb ? -(zj.y * inv) : 0.f;
-        x[P(j)] = make_float2(naj, nbj);
-        if (jr != j) x[P(jr)] = make_float2(nar, nbr);
+        z[P(j)] = make_float2(naj, nbj);
+        if (jr != j) z[P(jr)] = make_float2(nar, nbr);
         // odd: f1plus += N_i; even: f1min -= N_i(-t) = theta s(t)
         if (ina) {
           f1[ba + j] = haj + (odd ? naj : -nar);
@@ -514,7 +586,13 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       }
       __syncthreads();
       // 4. forward transform of N_i, band spectra into the stage rows of this pair
-      forward_band_stage<NT, THREADS>(s, x, tw, ra, rb, hasb);
+      float2* w = z;
+      if constexpr (kPingPong) {
+        w = fft_smem_pp<NT, THREADS, false>(z, z == x ? y : x, tw);
+      } else {
+        fft_smem<NT, THREADS, false>(z, tw);
+      }
+      unpack_band_stage<NT, THREADS>(s, w, ra, rb, hasb);
       // 5. per-trace energies
       block_sum2<THREADS>(ea, eb, red);
       if (threadIdx.x == 0) {
@@ -808,8 +886,12 @@ template <int NT>
 cudaError_t launch_epi_nt(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
   size_t bytes = 0;
   int G = epi_pairs<NT>(s.nw, &bytes);
-  // few traces: smaller blocks so that every SM gets work
-  while (G > 1 && (s.ncols + 2 * G - 1) / (2 * G) < epi_ctas(NT) * num_sms) G /= 2;
+  if (s.epi_g > 0) {
+    while (G > s.epi_g) G /= 2;  // a tuned choice, never above the shared-memory fit
+  } else {
+    // few traces: smaller blocks so that every SM gets work
+    while (G > 1 && (s.ncols + 2 * G - 1) / (2 * G) < epi_ctas(NT) * num_sms) G /= 2;
+  }
   bytes = epi_base_bytes(NT) + 2 * (size_t)G * (size_t)(s.nw | 1) * sizeof(float2);
   const int nblocks = (s.ncols + 2 * G - 1) / (2 * G);
   int grid = num_sms * epi_ctas(NT);
@@ -853,6 +935,17 @@ cudaError_t prepare_kernels() {
   MK_ATTR(4096) MK_ATTR(8192)
 #undef MK_ATTR
   return cudaSuccess;
+}
+
+int epilogue_max_pairs(int nt, int nw) {
+  size_t bytes = 0;
+  switch (nt) {
+#define MK_FIT(N) \
+  case N: return epi_pairs<N>(nw, &bytes);
+    MK_FIT(32) MK_FIT(64) MK_FIT(128) MK_FIT(256) MK_FIT(512) MK_FIT(1024) MK_FIT(2048) MK_FIT(4096) MK_FIT(8192)
+#undef MK_FIT
+    default: return 1;
+  }
 }
 
 bool epilogue_fits(int nt, int nw) {

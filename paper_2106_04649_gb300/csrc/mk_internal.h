@@ -51,6 +51,7 @@ struct SurveyDev {
   const float2* tw;   // [nt] e^{-2 pi i q / nt}
   int* err;           // device error word (bounded waits that ran out); may be null
   int* iter;          // device iteration index (parity and energy slot; advanced by the epilogue)
+  int epi_g;          // epilogue pairs per block: 0 = chosen from shared memory and grid size, else 1, 2 or 4
 };
 
 // Kernel launchers (return the launch status; the caller checks it).
@@ -67,6 +68,9 @@ cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t ro
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
 cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);
 bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the per-CTA limit
+int epilogue_max_pairs(int nt, int nw);  // largest pairs-per-block the epilogue's shared memory allows
+bool umma_set_bn(UmmaMaps* mp, const SurveyDev& s, int bn);  // N tile of the tensor-core contraction
+int umma_get_bn(const UmmaMaps* mp);
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);
 cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms);  // band spectrum of a field
 cudaError_t launch_inverse(const SurveyDev& s, float* dst, int mode, cudaStream_t st, int num_sms);

@@ -488,6 +488,20 @@ UmmaMaps* umma_create(const SurveyDev& s) {
 
 void umma_destroy(UmmaMaps* mp) { delete mp; }
 
+bool umma_set_bn(UmmaMaps* mp, const SurveyDev& s, int bn) {
+  if (!mp || (bn != 16 && bn != 32 && bn != 64 && bn != 128)) return false;
+  const int kp = 2 * s.r_pad;
+  UmmaMaps t = *mp;
+  t.bn = bn;
+  const bool ok = encode_map(&t.b0, s.Bq0, kp, 2 * s.F, s.nw, bn, t.fmt) &&
+                  encode_map(&t.b1, s.Bq1, kp, 2 * s.F, s.nw, bn, t.fmt) &&
+                  encode_map(&t.b2, t.nb >= 3 ? s.Bq2 : s.Bq1, kp, 2 * s.F, s.nw, bn, t.fmt);
+  if (ok) *mp = t;
+  return ok;
+}
+
+int umma_get_bn(const UmmaMaps* mp) { return mp ? mp->bn : 0; }
+
 cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms) {
   if (!mp) return cudaErrorInvalidValue;
   // the split forms target FP32-level accuracy: they promote per K block

@@ -45,6 +45,7 @@ def test_desc_layout_matches_c():
     # int32 x4, double x3, int32, uint32 -> 48 bytes with natural alignment
     assert ctypes.sizeof(N.MkDesc) == 48
     assert ctypes.sizeof(N.MkStats) == 64
+    assert ctypes.sizeof(N.MkTuning) == 24
 
 
 def test_workspace_size_and_validation_without_gpu():
