@@ -929,6 +929,7 @@ cudaError_t launch_init_nt(const SurveyDev& s, const float* Gd, cudaStream_t st,
 cudaError_t prepare_kernels() {
   cudaError_t e = prepare_contract();
   if (e != cudaSuccess) return e;
+  if ((e = prepare_load()) != cudaSuccess) return e;
 #define MK_ATTR(N) \
   if ((e = set_attrs<N>()) != cudaSuccess) return e;
   MK_ATTR(32) MK_ATTR(64) MK_ATTR(128) MK_ATTR(256) MK_ATTR(512) MK_ATTR(1024) MK_ATTR(2048)

@@ -62,6 +62,7 @@ void umma_destroy(UmmaMaps* mp);
 cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms);
 cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st, int num_sms, int* nlaunch);
 // R row loads (grid-stride, at most max_blocks blocks of 256 threads)
+cudaError_t prepare_load();
 cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
                                int max_blocks);
 // Energies of iteration i go to ring[(i % slots) * F + f].

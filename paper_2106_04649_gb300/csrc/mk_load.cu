@@ -43,6 +43,18 @@ __global__ void __launch_bounds__(256) load_rows_c64_kernel(const float2* __rest
 
 }  // namespace
 
+// The row loads run beside the contraction and the epilogue when R is loaded
+// asynchronously: they ask for the shared-memory-heavy carveout those kernels
+// use, so that an SM can hold both (kernels whose carveouts differ cannot
+// share an SM until it drains).
+cudaError_t prepare_load() {
+  cudaError_t e = cudaFuncSetAttribute(load_rows_c64_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(load_rows_q_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
+}
+
 cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
                                int max_blocks) {
   int64_t grid = (rows + 7) / 8;
