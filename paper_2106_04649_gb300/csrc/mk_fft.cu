@@ -146,25 +146,26 @@ __device__ __forceinline__ void stockham_pass(float2* x, const float2* tw, int N
   __syncthreads();
 }
 
-// The same pass out of place: reads in, writes out, one barrier.  The pass
-// before wrote in and read out before its own barrier, so nothing else
-// orders the two.
-template <int NT, int THREADS, bool INV, int R>
-__device__ __forceinline__ void stockham_pass_pp(const float2* in, float2* out, const float2* tw, int Ns, int toff) {
+// The same pass out of place, with the sub-length NS known at compile
+// time (index and twiddle offsets fold into constants): reads in, writes
+// out, one barrier.  The pass before wrote in and read out before its own
+// barrier, so nothing else orders the two.
+template <int NT, int THREADS, bool INV, int R, int NS>
+__device__ __forceinline__ void stockham_pass_pp(const float2* in, float2* out, const float2* tw) {
   constexpr int NB = NT / R;
   constexpr int PB = (NB + THREADS - 1) / THREADS;
 #pragma unroll
   for (int q = 0; q < PB; ++q) {
     const int j = threadIdx.x + q * THREADS;
     if (j < NB) {
-      const int k = j & (Ns - 1);
+      const int k = j & (NS - 1);
       float2 v[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = in[P(j + r * NB)];
-      if (Ns > 1) {
+      if constexpr (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          float2 w = tw[toff + (r - 1) * Ns + k];
+          float2 w = tw[(r - 1) * NS + k];
           if (INV) w.y = -w.y;
           v[r] = cmul(v[r], w);
         }
@@ -172,40 +173,38 @@ __device__ __forceinline__ void stockham_pass_pp(const float2* in, float2* out, 
       dftR<INV, R>(v);
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) out[P(base + r * Ns)] = v[r];
+      for (int r = 0; r < R; ++r) out[P(base + r * NS)] = v[r];
     }
   }
   __syncthreads();
 }
 
-// Complex DFT of a[P(0 .. NT-1)] ping-ponging between a and b; returns the
-// buffer that holds the result (a for an even number of passes).
-template <int NT, int THREADS, bool INV>
-__device__ __forceinline__ float2* fft_smem_pp(float2* a, float2* b, const float2* tw) {
+// Complex DFT of in[P(0 .. NT-1)] ping-ponging between in and out, one pass
+// per level of the compile-time recursion (radix-8 passes, then one radix-2
+// or radix-4 pass); returns the buffer that holds the result.  The twiddle
+// table holds the passes' tables back to back.
+template <int NT, int THREADS, bool INV, int PASS, int NS, int TOFF>
+__device__ __forceinline__ float2* fft_pp_from(float2* in, float2* out, const float2* tw) {
   constexpr int LOG2 = ilog2(NT);
   constexpr int N8 = LOG2 / 3;
   constexpr int REM = LOG2 % 3;
-  int Ns = 1, toff = 0;
-  float2* in = a;
-  float2* out = b;
-#pragma unroll 1
-  for (int p = 0; p < N8; ++p) {
-    stockham_pass_pp<NT, THREADS, INV, 8>(in, out, tw, Ns, toff);
-    toff += 7 * Ns;
-    Ns *= 8;
-    float2* t = in;
-    in = out;
-    out = t;
+  if constexpr (PASS < N8) {
+    stockham_pass_pp<NT, THREADS, INV, 8, NS>(in, out, tw + TOFF);
+    return fft_pp_from<NT, THREADS, INV, PASS + 1, NS * 8, TOFF + 7 * NS>(out, in, tw);
+  } else if constexpr (REM == 1) {
+    stockham_pass_pp<NT, THREADS, INV, 2, NS>(in, out, tw + TOFF);
+    return out;
+  } else if constexpr (REM == 2) {
+    stockham_pass_pp<NT, THREADS, INV, 4, NS>(in, out, tw + TOFF);
+    return out;
+  } else {
+    return in;
   }
-  if (REM == 1) {
-    stockham_pass_pp<NT, THREADS, INV, 2>(in, out, tw, Ns, toff);
-    in = out;
-  }
-  if (REM == 2) {
-    stockham_pass_pp<NT, THREADS, INV, 4>(in, out, tw, Ns, toff);
-    in = out;
-  }
-  return in;
+}
+
+template <int NT, int THREADS, bool INV>
+__device__ __forceinline__ float2* fft_smem_pp(float2* a, float2* b, const float2* tw) {
+  return fft_pp_from<NT, THREADS, INV, 0, 1, 0>(a, b, tw);
 }
 
 // In-place complex DFT of x[P(0 .. NT-1)] (unnormalised; sign -1 forward,
