@@ -170,20 +170,42 @@ def roofline_for(s, F, rprec, c_ms):
                 "frac": ach / peaks["hbm_gbs"], "traffic": profiled_traffic(key),
                 "kernel": "gemv_bulk_kernel (complex GEMV)", "peak_source": f"{kind} hbm_gbs (copy)",
                 "algorithmic_bytes_per_launch": b, "algorithmic_flops_per_launch": flops, "avg_launch_ms": c_ms}
+    # F > 1: the binding roof is the larger of two lower bounds on the launch time,
+    # the algorithmic DRAM bytes (R, the field spectrum operand and S, each moved
+    # once) at the measured copy bandwidth, and the algorithmic flops at the
+    # compute peak of the form
+    s_bytes = n_w * n * F * 8
     if rprec == "c64":
-        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        ach = flops / (c_ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": profiled_traffic(key), "kernel": "cgemm_f32_kernel (SIMT FP32 complex GEMM)",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                "algorithmic_flops_per_launch": flops, "avg_launch_ms": c_ms}
-    tflops = NPROD[RPREC[rprec]] * flops
-    peak = peaks["bf16_tflops_sustained"]
-    ach = tflops / (c_ms * 1e-3) / 1e12
-    return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": profiled_traffic(key), "kernel": f"umma_cgemm_kernel (tcgen05, {rprec}, "
-            f"{NPROD[RPREC[rprec]]} products)", "peak_source": f"{kind} bf16_tflops_sustained (cuBLAS)",
-            "algorithmic_flops_per_launch": tflops, "avg_launch_ms": c_ms}
+        peak_c = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        work = flops
+        b = n_w * n * n * 8 + n_w * F * n * 8 + s_bytes
+        comp = {"bound": "alu", "unit": "TFLOP/s", "peak": peak_c,
+                "kernel": "cgemm_f32_wide_kernel (SIMT FP32 complex GEMM)" if n >= 128 else
+                          "cgemm_f32_kernel (SIMT FP32 complex GEMM)",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        nb = 3 if rprec == "split3" else 2   # 16-bit parts of the field embedding
+        peak_c = peaks["bf16_tflops_sustained"]
+        work = NPROD[RPREC[rprec]] * flops
+        b = n_w * n * n * RBYTES[rprec] + n_w * 2 * F * 2 * n * 2 * nb + s_bytes
+        comp = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak_c,
+                "kernel": f"umma_cgemm_kernel (tcgen05, {rprec}, {NPROD[RPREC[rprec]]} products)",
+                "peak_source": f"{kind} bf16_tflops_sustained (cuBLAS)"}
+    t_hbm = b / (peaks["hbm_gbs"] * 1e9)
+    t_comp = work / (peak_c * 1e12)
+    out = {"traffic": profiled_traffic(key), "algorithmic_bytes_per_launch": b,
+           "algorithmic_flops_per_launch": work, "avg_launch_ms": c_ms,
+           "lower_bounds_ms": {"hbm": 1e3 * t_hbm, comp["bound"]: 1e3 * t_comp}}
+    if t_hbm > t_comp:
+        ach = b / (c_ms * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "kernel": comp["kernel"],
+                    "peak_source": f"{kind} hbm_gbs (copy)"})
+    else:
+        ach = work / (c_ms * 1e-3) / 1e12
+        out.update({"bound": comp["bound"], "achieved": ach, "peak": peak_c, "unit": "TFLOP/s",
+                    "frac": ach / peak_c, "kernel": comp["kernel"], "peak_source": comp["peak_source"]})
+    return out
 
 
 # --------------------------------------------------------------------------- CPU oracle
