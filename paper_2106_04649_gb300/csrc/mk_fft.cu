@@ -386,8 +386,9 @@ __device__ __forceinline__ int stage_ld(int nw) { return nw | 1; }
 // Resident epilogue CTAs per SM the launch is built for (registers and
 // shared memory are sized to fit that many).
 __host__ __device__ constexpr int epi_ctas(int nt) { return nt <= 2048 ? 2 : 1; }
+__host__ __device__ constexpr int epi_threads(int nt) { return threads_for(nt); }
 __host__ __device__ constexpr size_t epi_smem_target(int nt) {
-  return epi_ctas(nt) >= 3 ? 73 * 1024 : 113 * 1024;
+  return epi_ctas(nt) >= 4 ? 55 * 1024 : (epi_ctas(nt) >= 3 ? 73 * 1024 : 113 * 1024);
 }
 
 // The f1 window samples of a pair are prefetched into shared memory (2 NT
@@ -444,9 +445,9 @@ __device__ __forceinline__ void unpack_band_stage(const SurveyDev& s, const floa
 }
 
 template <int NT>
-__global__ void __launch_bounds__(threads_for(NT), epi_ctas(NT))
+__global__ void __launch_bounds__(epi_threads(NT), epi_ctas(NT))
 epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
-  constexpr int THREADS = threads_for(NT);
+  constexpr int THREADS = epi_threads(NT);
   extern __shared__ float4 smem_raw[];
   constexpr bool kPingPong = epi_pingpong(NT);
   float2* x = reinterpret_cast<float2*>(smem_raw);  // the pair: s, then N_i, then its transform
@@ -895,7 +896,7 @@ cudaError_t launch_epi_nt(const SurveyDev& s, double* ring, int slots, cudaStrea
   const int nblocks = (s.ncols + 2 * G - 1) / (2 * G);
   int grid = num_sms * epi_ctas(NT);
   if (grid > nblocks) grid = nblocks;
-  epilogue_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, ring, slots, G);
+  epilogue_kernel<NT><<<grid, epi_threads(NT), bytes, st>>>(s, ring, slots, G);
   return cudaGetLastError();
 }
 
