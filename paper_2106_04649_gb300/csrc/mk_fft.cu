@@ -227,49 +227,30 @@ __device__ __forceinline__ void fft_smem(float2* x, const float2* tw) {
   if (REM == 2) stockham_pass<NT, THREADS, INV, 4>(x, tw, Ns, toff);
 }
 
-// Block-wide sum of two doubles in a fixed order (deterministic).
-template <int THREADS>
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* red) {
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_down_sync(0xffffffffu, a, o);
-    b += __shfl_down_sync(0xffffffffu, b, o);
-  }
-  constexpr int NWARP = THREADS / 32;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[2 * wid] = a;
-    red[2 * wid + 1] = b;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double sa = 0.0, sb = 0.0;
-    for (int w = 0; w < NWARP; ++w) {
-      sa += red[2 * w];
-      sb += red[2 * w + 1];
-    }
-    a = sa;
-    b = sb;
-  }
-  __syncthreads();
-}
-
 __device__ __forceinline__ int64_t field_offset(const SurveyDev& s, int t) { return (int64_t)t * s.nt; }
 
-// Two 16-bit values packed in 32 bits (low half first in memory).
+// (a, b) rounded to 16 bits (nearest even) as one packed pair; their values
+// back in FP32 in ra, rb.
 template <bool BF16>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
+__device__ __forceinline__ uint32_t round_pair(float a, float b, float& ra, float& rb) {
   if (BF16) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    const float2 f = __bfloat1622float2(v);
+    ra = f.x;
+    rb = f.y;
     return *reinterpret_cast<const uint32_t*>(&v);
   } else {
     const __half2 v = __floats2half2_rn(a, b);
+    const float2 f = __half22float2(v);
+    ra = f.x;
+    rb = f.y;
     return *reinterpret_cast<const uint32_t*>(&v);
   }
 }
-template <bool BF16>
-__device__ __forceinline__ float round16(float a) {
-  return BF16 ? __bfloat162float(__float2bfloat16_rn(a)) : __half2float(__float2half_rn(a));
-}
+// From the packed pair (x, y): (x, -y) flips the sign bit of the upper half,
+// (y, x) swaps the halves.
+__device__ __forceinline__ uint32_t pair_neg_hi(uint32_t w) { return w ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t pair_swap(uint32_t w) { return __byte_perm(w, 0, 0x1032); }
 
 // Band value N = (nr, ni) of trace t at bin m into the K-major real
 // embedding of the tensor-core contraction, split into hi + lo 16-bit parts:
@@ -280,22 +261,28 @@ __device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int f
   const int64_t e0 = ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k;
   uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
   uint32_t* b1 = reinterpret_cast<uint32_t*>(s.Bq1);
-  const float hr = round16<BF16>(nr), hi = round16<BF16>(ni);
+  float hr, hi;
+  const uint32_t h = round_pair<BF16>(nr, ni, hr, hi);
   float lr = nr - hr, li = ni - hi;  // exact in FP32
-  b0[e0 >> 1] = pack2<BF16>(hr, -hi);
-  b0[(e0 + kp) >> 1] = pack2<BF16>(hi, hr);
+  b0[e0 >> 1] = pair_neg_hi(h);
+  b0[(e0 + kp) >> 1] = pair_swap(h);
   if (s.rprec == 4) {  // 3-way split: hi, mid = rn(x - hi), lo = rn(x - hi - mid)
-    const float mr = round16<BF16>(lr), mi = round16<BF16>(li);
-    b1[e0 >> 1] = pack2<BF16>(mr, -mi);
-    b1[(e0 + kp) >> 1] = pack2<BF16>(mi, mr);
+    float mr, mi;
+    const uint32_t md = round_pair<BF16>(lr, li, mr, mi);
+    b1[e0 >> 1] = pair_neg_hi(md);
+    b1[(e0 + kp) >> 1] = pair_swap(md);
     lr -= mr;
     li -= mi;
     uint32_t* b2 = reinterpret_cast<uint32_t*>(s.Bq2);
-    b2[e0 >> 1] = pack2<BF16>(lr, -li);
-    b2[(e0 + kp) >> 1] = pack2<BF16>(li, lr);
+    float dr, di;
+    const uint32_t lo = round_pair<BF16>(lr, li, dr, di);
+    b2[e0 >> 1] = pair_neg_hi(lo);
+    b2[(e0 + kp) >> 1] = pair_swap(lo);
   } else {
-    b1[e0 >> 1] = pack2<BF16>(lr, -li);
-    b1[(e0 + kp) >> 1] = pack2<BF16>(li, lr);
+    float dr, di;
+    const uint32_t lo = round_pair<BF16>(lr, li, dr, di);
+    b1[e0 >> 1] = pair_neg_hi(lo);
+    b1[(e0 + kp) >> 1] = pair_swap(lo);
   }
 }
 
@@ -457,7 +444,8 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   const int ld = stage_ld(s.nw);
   constexpr bool kPrefetch = epi_prefetch(NT);
   float* hbuf = reinterpret_cast<float*>(stage + 2 * G * ld);  // [2][NT] f1 window samples (2G ld is even: 16-byte aligned)
-  __shared__ double red[2 * (THREADS / 32)];
+  constexpr int kWarps = THREADS / 32;
+  __shared__ double ered[8 * kWarps];  // per-warp energy sums of the block's traces (at most 8)
   __shared__ int s_last;
 
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
@@ -593,13 +581,23 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
         fft_smem<NT, THREADS, false>(z, tw);
       }
       unpack_band_stage<NT, THREADS>(s, w, ra, rb, hasb);
-      // 5. per-trace energies
-      block_sum2<THREADS>(ea, eb, red);
-      if (threadIdx.x == 0) {
-        s.Epart[t0] = ea;
-        if (hasb) s.Epart[t0 + 1] = eb;
+      // 5. per-trace energies: warp sums here (fixed shuffle tree), the sum
+      //    over warps in warp order once the block is done
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ea += __shfl_down_sync(0xffffffffu, ea, o);
+        eb += __shfl_down_sync(0xffffffffu, eb, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        ered[(2 * q) * kWarps + (threadIdx.x >> 5)] = ea;
+        ered[(2 * q + 1) * kWarps + (threadIdx.x >> 5)] = eb;
       }
       __syncthreads();
+    }
+    if (threadIdx.x < ntr) {
+      double e = 0.0;
+      for (int w = 0; w < kWarps; ++w) e += ered[threadIdx.x * kWarps + w];
+      s.Epart[tb + threadIdx.x] = e;
     }
     // 6. the block's new band spectra, one coalesced pass
     if (cc < ntr) {
