@@ -446,6 +446,7 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   float* hbuf = reinterpret_cast<float*>(stage + 2 * G * ld);  // [2][NT] f1 window samples (2G ld is even: 16-byte aligned)
   constexpr int kWarps = THREADS / 32;
   __shared__ double ered[8 * kWarps];  // per-warp energy sums of the block's traces (at most 8)
+  __shared__ int sL[8];                // window half-lengths of the block's traces
   __shared__ int s_last;
 
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
@@ -480,14 +481,15 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       }
       for (; m < s.nw; m += mstep) dst[m] = __ldg(src + (int64_t)m * s.s_stride);
     }
+    if (threadIdx.x < ntr) sL[threadIdx.x] = s.L[tb + threadIdx.x];  // the block's window lengths
     __syncthreads();
     for (int q = 0; 2 * q < ntr; ++q) {
       const int t0 = tb + 2 * q;
       const bool hasb = 2 * q + 1 < ntr;
       float2* ra = stage + (2 * q) * ld;
       float2* rb = ra + ld;
-      const int La = s.L[t0];
-      const int Lb = hasb ? s.L[t0 + 1] : 0;
+      const int La = sL[2 * q];
+      const int Lb = hasb ? sL[2 * q + 1] : 0;
       const int64_t ba = field_offset(s, t0);
       const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
       if constexpr (kPrefetch) {
