@@ -7,15 +7,16 @@
 // one pass: R is read from HBM exactly once per iteration, the field
 // spectrum stays on chip, and a warp-shuffle tree reduces each row.
 //
-// Main kernel (gemv_bulk_kernel): each CTA (one per SM) owns a contiguous
-// range of rows (m, k) of the frequency-major R and streams it through a
-// ring of shared-memory stages filled by bulk asynchronous copies
-// (cp.async.bulk + mbarrier), so that ~190 KB per SM are in flight; one
-// producer lane issues the copies, eight consumer warps each reduce one row
-// per stage with 128-bit shared loads, their slice of Nw_m held in registers
-// (reloaded only when m changes), and a warp-shuffle tree.  Every wait is
-// bounded: on time-out the kernel drains its copies, sets an error word and
-// returns.  Rows too long for the ring use the register-streaming kernels.
+// Main kernel (gemv_bulk_kernel): one CTA per SM streams units of up to 64
+// rows (m, k) of one frequency of the frequency-major R, taken from a global
+// work counter, through a ring of shared-memory stages filled by bulk
+// asynchronous copies (cp.async.bulk + mbarrier), so that ~190 KB per SM are
+// in flight; one producer lane issues the copies, eight consumer warps each
+// reduce one row per stage with 128-bit shared loads, their slice of Nw_m
+// held in registers (reloaded only when m changes), and a warp-shuffle tree.
+// Every wait is bounded: on time-out the kernel drains its copies, sets an
+// error word and finishes.  Rows too long for the ring use the
+// register-streaming kernels.
 
 #include "mk_internal.h"
 
@@ -165,18 +166,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
+constexpr int kUnitRows = 64;  // rows per work unit, all of one frequency (8 stages of 8 rows)
+
+// Work is handed out dynamically: the producer lane takes units of up to 64
+// rows of one frequency from a global counter, so SMs that stream faster take
+// more units and all finish together.  A stage records its first row and row
+// count; a stage without rows ends the stream.  The last CTA to finish
+// resets the counters (queue[0]: next unit, queue[1]: finished CTAs), so
+// every launch starts from zero; no thread leaves before the final barrier.
 template <int PER>
 __global__ void __launch_bounds__(kBulkThreads, 1)
 gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S, int ns,
-                 int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows, int stages,
-                 int* __restrict__ err) {
+                 int rq, int64_t nw_stride4, int64_t s_stride, float c, int nw, int stages,
+                 unsigned* __restrict__ queue, int* __restrict__ err) {
   extern __shared__ __align__(128) float4 ring[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
+  __shared__ int64_t st_row[kMaxStages];  // first row m * ns + k of a stage; -1 ends the stream
+  __shared__ int st_n[kMaxStages];        // rows in a stage
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * total_rows / gridDim.x;
-  const int64_t row1 = (int64_t)(blockIdx.x + 1) * total_rows / gridDim.x;
-  const int64_t ngroups = (row1 - row0 + kConsWarps - 1) / kConsWarps;
+  const int upf = (ns + kUnitRows - 1) / kUnitRows;  // units per frequency
+  const int nunits = nw * upf;
   const int stage_f4 = kConsWarps * rq;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -187,81 +197,108 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
   }
   __syncthreads();
 
-  if (warp == kConsWarps) {  // producer: one lane issues the bulk copies
+  if (warp == kConsWarps) {  // producer: one lane takes units and issues the bulk copies
     if (lane == 0) {
       bool ok = true;
-      int64_t g = 0;
-      for (; g < ngroups; ++g) {
-        const int s = (int)(g % stages);
-        const uint32_t ph = (uint32_t)((g / stages) & 1);
-        if (!mbar_wait_bounded(smem_u32(&empty_bar[s]), ph ^ 1u)) {
-          ok = false;
-          break;
+      uint32_t it = 0;
+      for (;;) {
+        const int u = (int)atomicAdd(queue, 1u);
+        if (u >= nunits) break;
+        const int m = u / upf;
+        const int k0 = (u - m * upf) * kUnitRows;
+        const int kn = ns - k0 < kUnitRows ? ns - k0 : kUnitRows;
+        for (int g = 0; g < kn; g += kConsWarps, ++it) {
+          const int s = (int)(it % stages);
+          if (!mbar_wait_bounded(smem_u32(&empty_bar[s]), ((it / stages) & 1u) ^ 1u)) {
+            ok = false;
+            break;
+          }
+          const int nrows = kn - g < kConsWarps ? kn - g : kConsWarps;
+          const int64_t row = (int64_t)m * ns + k0 + g;
+          st_row[s] = row;
+          st_n[s] = nrows;
+          const uint32_t bytes = (uint32_t)nrows * (uint32_t)rq * 16u;
+          mbar_expect_tx(smem_u32(&full_bar[s]), bytes);
+          bulk_g2s(smem_u32(ring + (size_t)s * stage_f4), R + row * rq, bytes, smem_u32(&full_bar[s]));
         }
-        const int64_t r = row0 + g * kConsWarps;
-        const int64_t left = row1 - r;
-        const int nrows = left < kConsWarps ? (int)left : kConsWarps;
-        const uint32_t bytes = (uint32_t)nrows * (uint32_t)rq * 16u;
-        mbar_expect_tx(smem_u32(&full_bar[s]), bytes);
-        bulk_g2s(smem_u32(ring + (size_t)s * stage_f4), R + r * rq, bytes, smem_u32(&full_bar[s]));
+        if (!ok) break;
+      }
+      if (ok) {  // end of the stream: a stage without rows
+        const int s = (int)(it % stages);
+        if (mbar_wait_bounded(smem_u32(&empty_bar[s]), ((it / stages) & 1u) ^ 1u)) {
+          st_row[s] = -1;
+          st_n[s] = 0;
+          mbar_arrive(smem_u32(&full_bar[s]));
+          ++it;
+        } else {
+          ok = false;
+        }
       }
       // no copy may still be in flight when the CTA exits
-      for (int64_t q = (g > stages ? g - stages : 0); q < g; ++q) {
-        if (!mbar_wait_bounded(smem_u32(&full_bar[q % stages]), (uint32_t)((q / stages) & 1))) ok = false;
+      for (uint32_t q = (it > (uint32_t)stages ? it - stages : 0); q < it; ++q) {
+        if (!mbar_wait_bounded(smem_u32(&full_bar[q % stages]), (q / stages) & 1u)) ok = false;
       }
       if (!ok && err) atomicExch(err, 1);
     }
-    return;
-  }
-
-  // consumers: warp w reduces row w of every stage
-  int cur_w = -1;
-  float4 nv[PER];
-  for (int64_t g = 0; g < ngroups; ++g) {
-    const int s = (int)(g % stages);
-    const uint32_t ph = (uint32_t)((g / stages) & 1);
-    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&full_bar[s]), ph));
-    if (!ok) {
-      if (lane == 0 && err) atomicExch(err, 2);
-      return;
-    }
-    const int64_t row = row0 + g * kConsWarps + warp;
-    if (row < row1) {
-      const int w = (int)(row / ns);
-      const int k = (int)(row - (int64_t)w * ns);
-      if (w != cur_w) {
-        const float4* nrow = Nw + (int64_t)w * nw_stride4;
+  } else {
+    // consumers: warp w reduces row w of every stage
+    int cur_w = -1;
+    float4 nv[PER];
+    for (uint32_t it = 0;; ++it) {
+      const int s = (int)(it % stages);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&full_bar[s]), (it / stages) & 1u));
+      if (!ok) {
+        if (lane == 0 && err) atomicExch(err, 2);
+        break;
+      }
+      const int64_t row0 = st_row[s];
+      if (row0 < 0) break;
+      if (warp < st_n[s]) {
+        const int64_t row = row0 + warp;
+        const int w = (int)(row / ns);
+        const int k = (int)(row - (int64_t)w * ns);
+        if (w != cur_w) {
+          const float4* nrow = Nw + (int64_t)w * nw_stride4;
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const int i = lane + 32 * q;
+            nv[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+          cur_w = w;
+        }
+        const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
+        float re = 0.f, im = 0.f;
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
           const int i = lane + 32 * q;
-          nv[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+          re = fmaf(rv.x, nv[q].x, re);
+          re = fmaf(-rv.y, nv[q].y, re);
+          re = fmaf(rv.z, nv[q].z, re);
+          re = fmaf(-rv.w, nv[q].w, re);
+          im = fmaf(rv.x, nv[q].y, im);
+          im = fmaf(rv.y, nv[q].x, im);
+          im = fmaf(rv.z, nv[q].w, im);
+          im = fmaf(rv.w, nv[q].z, im);
         }
-        cur_w = w;
-      }
-      const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
-      float re = 0.f, im = 0.f;
 #pragma unroll
-      for (int q = 0; q < PER; ++q) {
-        const int i = lane + 32 * q;
-        const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        re = fmaf(rv.x, nv[q].x, re);
-        re = fmaf(-rv.y, nv[q].y, re);
-        re = fmaf(rv.z, nv[q].z, re);
-        re = fmaf(-rv.w, nv[q].w, re);
-        im = fmaf(rv.x, nv[q].y, im);
-        im = fmaf(rv.y, nv[q].x, im);
-        im = fmaf(rv.z, nv[q].w, im);
-        im = fmaf(rv.w, nv[q].z, im);
+        for (int o = 16; o > 0; o >>= 1) {
+          re += __shfl_xor_sync(0xffffffffu, re, o);
+          im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        re += __shfl_xor_sync(0xffffffffu, re, o);
-        im += __shfl_xor_sync(0xffffffffu, im, o);
-      }
-      if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+      atomicExch(queue, 0u);
+      atomicExch(queue + 1, 0u);
+    }
   }
 }
 
@@ -276,12 +313,11 @@ cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   const int rq = s.r_pad / 2;
   const int stages = bulk_stages(rq);
   const size_t smem = (size_t)stages * kConsWarps * rq * 16;
-  const int64_t total = (int64_t)s.nw * s.ns;
-  int64_t grid = num_sms;
-  if (grid * kConsWarps > total) grid = (total + kConsWarps - 1) / kConsWarps;
+  const int64_t units = (int64_t)s.nw * ((s.ns + kUnitRows - 1) / kUnitRows);
+  const int64_t grid = units < num_sms ? units : num_sms;
   gemv_bulk_kernel<PER><<<(unsigned)grid, kBulkThreads, smem, st>>>(
       reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq,
-      s.nw_stride / 2, s.s_stride, s.c, total, stages, s.err);
+      s.nw_stride / 2, s.s_stride, s.c, s.nw, stages, s.counter + 1, s.err);
   return cudaGetLastError();
 }
 
