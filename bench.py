@@ -157,6 +157,24 @@ def profiled_traffic(workload_key: str):
     return e.get("dram_bytes_per_launch")
 
 
+def lower_bound_ms(s, F, rprec):
+    """Roof of one contraction launch: (bound, ms), the larger of the algorithmic DRAM
+    bytes at the measured copy bandwidth and the algorithmic flops at the form's peak."""
+    peaks, _ = measured_peaks()
+    n_w, n = s.nw, s.n
+    flops = 8.0 * n_w * n * n * F
+    if rprec == "c64":
+        b = n_w * n * n * 8 + n_w * F * n * 8 + n_w * n * F * 8
+        work, peak, name = flops, SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12, "alu"
+    else:
+        nb = 3 if rprec == "split3" else 2
+        b = n_w * n * n * RBYTES[rprec] + n_w * 2 * F * 2 * n * 2 * nb + n_w * n * F * 8
+        work, peak, name = NPROD[RPREC[rprec]] * flops, peaks["bf16_tflops_sustained"], "tensor"
+    t_hbm = b / (peaks["hbm_gbs"] * 1e9)
+    t_comp = work / (peak * 1e12)
+    return ("hbm", 1e3 * t_hbm) if t_hbm > t_comp else (name, 1e3 * t_comp)
+
+
 def roofline_for(s, F, rprec, c_ms):
     """Roofline object of the dominant kernel (the contraction) from its mean launch time."""
     peaks, kind = measured_peaks()
@@ -475,10 +493,16 @@ def main_ours(args):
         br = Runner(items, dev, local)
         bms, bst, _ = br.timed(5, 2)
         br.close()
+        # aggregate roofline: each survey's contraction roof (its own bound), summed, over the
+        # summed measured contraction time
+        roof_ms = NITER * sum(lower_bound_ms(x, x.nfocal, rp)[1] for x, rp in items)
         variants.append({"workload": "batching: 12 surveys, n 201-1201, nt 1024-4096, 1-256 focal points, "
                                      "even surveys c64, odd surveys split3, one plan, stream launches", "nfocal": br.F,
                          "value": br.F * 5 / (bms / 1e3), "ms_per_step": bms / 5,
                          "contract_ms_total": bst["contract_ms"] / 5, "epilogue_ms_total": bst["epilogue_ms"] / 5,
+                         "contraction_roofline_frac": roof_ms / (bst["contract_ms"] / 5),
+                         "contraction_bounds": {b: sum(1 for x, rp in items if lower_bound_ms(x, x.nfocal, rp)[0] == b)
+                                                for b in ("hbm", "alu", "tensor")},
                          "gpu_launches_per_step": bst["launches"] / 5})
         gr = Runner(items, dev, local, timing=False, graph=True)
         gms, gst, _ = gr.timed(5, 2)
