@@ -192,7 +192,7 @@ size_t layout(Survey& sv, char* base) {
   v.L = reinterpret_cast<int*>(take((size_t)(v.ncols + 1) * sizeof(int)));
   v.td = reinterpret_cast<double*>(take((size_t)v.ncols * sizeof(double)));
   v.Epart = reinterpret_cast<double*>(take((size_t)(v.ncols + 1) * sizeof(double)));
-  v.counter = reinterpret_cast<unsigned*>(take(4 * sizeof(unsigned)));
+  v.counter = reinterpret_cast<unsigned*>(take(8 * sizeof(unsigned)));
   v.err = reinterpret_cast<int*>(take(sizeof(int)));
   v.iter = reinterpret_cast<int*>(take(sizeof(int)));
   v.tw = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));

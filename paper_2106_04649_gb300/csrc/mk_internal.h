@@ -47,7 +47,8 @@ struct SurveyDev {
   int* L;           // [ncols] window half-lengths
   double* td;       // [F][ns] staging of t_d uploaded from the host
   double* Epart;    // [ncols + 1] per-trace energies
-  unsigned* counter;  // [4]: last-block counter of the epilogue; work counter and finished CTAs of the GEMV
+  unsigned* counter;  // [8]: epilogue last-CTA count; GEMV work counter and finished CTAs (1, 2);
+                      // tensor-core contraction work counter and finished CTAs (4, 5)
   const float2* tw;   // [nt] e^{-2 pi i q / nt}
   int* err;           // device error word (bounded waits that ran out); may be null
   int* iter;          // device iteration index (parity and energy slot; advanced by the epilogue)

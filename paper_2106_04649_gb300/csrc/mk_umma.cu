@@ -66,7 +66,10 @@ struct UmmaParams {
   int64_t s_stride;
   float c;
   int* err;
+  unsigned* queue;  // [2]: next tile, finished CTAs (the last CTA resets both)
 };
+
+constexpr int kTQ = 4;  // tile-index slots between the producer and the MMA and epilogue warps
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -162,6 +165,9 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
   __shared__ __align__(8) uint64_t tfull[2];
   __shared__ __align__(8) uint64_t tempty[2];
   __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ __align__(8) uint64_t tq_full[kTQ];   // tile index written
+  __shared__ __align__(8) uint64_t tq_empty[kTQ];  // read by the MMA lane and the 4 epilogue warps
+  __shared__ int tq[kTQ];                           // tile index, -1 ends the work
   __shared__ uint32_t tmem_slot;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -179,6 +185,10 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
       mbar_init(smem_u32(&tempty[a]), 4);
     }
     mbar_init(smem_u32(&drain_bar), 1);
+    for (int q = 0; q < kTQ; ++q) {
+      mbar_init(smem_u32(&tq_full[q]), 1);
+      mbar_init(smem_u32(&tq_empty[q]), 5);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -196,7 +206,18 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
     if (lane == 0) {  // ------------------------------------------------ TMA producer
       bool ok = true;
       uint32_t it = 0;
-      for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
+      // tiles come from a work counter, so SMs that run faster take more of them
+      for (uint32_t tc = 0; ok; ++tc) {
+        const int q = (int)(tc % kTQ);
+        if (!mbar_wait(smem_u32(&tq_empty[q]), ((tc / kTQ) & 1u) ^ 1u)) {
+          ok = false;
+          break;
+        }
+        int tile = (int)atomicAdd(P.queue, 1u);
+        if (tile >= total_tiles) tile = -1;
+        tq[q] = tile;
+        mbar_arrive(smem_u32(&tq_full[q]));
+        if (tile < 0) break;
         const int m = tile / tiles_per_m;
         const int rem = tile - m * tiles_per_m;
         const int mt = rem / P.ntiles, nt = rem - (rem / P.ntiles) * P.ntiles;
@@ -227,8 +248,16 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
   } else if (warp == 1) {
     if (lane == 0) {  // ------------------------------------------------ MMA issuer
       bool ok = true;
-      uint32_t it = 0, tc = 0;
-      for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x, ++tc) {
+      uint32_t it = 0;
+      for (uint32_t tc = 0; ok; ++tc) {
+        const int q = (int)(tc % kTQ);
+        if (!mbar_wait(smem_u32(&tq_full[q]), (tc / kTQ) & 1u)) {
+          ok = false;
+          break;
+        }
+        const int tile = tq[q];
+        mbar_arrive(smem_u32(&tq_empty[q]));
+        if (tile < 0) break;
         uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
         if (!PROMOTE) {
           if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
@@ -290,8 +319,17 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
   } else {  // -------------------------------------------------------------- epilogue
     const int quad = warp & 3;  // TMEM lane quadrant this warp may access
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-    uint32_t tc = 0, it = 0;
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x, ++tc) {
+    uint32_t it = 0;
+    for (uint32_t tc = 0;; ++tc) {
+      const int q = (int)(tc % kTQ);
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&tq_full[q]), (tc / kTQ) & 1u))) {
+        if (lane == 0 && P.err) atomicExch(P.err, 14);
+        break;
+      }
+      const int tile = tq[q];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tq_empty[q]));
+      if (tile < 0) break;
       const int m = tile / tiles_per_m;
       const int rem = tile - m * tiles_per_m;
       const int mt = rem / P.ntiles, nt = rem - (rem / P.ntiles) * P.ntiles;
@@ -359,6 +397,13 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                  : "memory");
   }
+  if (threadIdx.x == 0) {  // the last CTA to finish resets the work counters
+    __threadfence();
+    if (atomicAdd(P.queue + 1, 1u) == gridDim.x - 1) {
+      atomicExch(P.queue, 0u);
+      atomicExch(P.queue + 1, 0u);
+    }
+  }
 }
 
 template <int BN, int NA, int NB>
@@ -384,6 +429,7 @@ cudaError_t launch_bn(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, i
   P.s_stride = s.s_stride;
   P.c = s.c;
   P.err = s.err;
+  P.queue = s.counter + 4;
   const int64_t tiles = (int64_t)P.nw * P.mtiles * P.ntiles;
   const int grid = (int)(tiles < num_sms ? tiles : num_sms);
   umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE><<<grid, kThreads, smem, st>>>(mp.a0, mp.a1, mp.a2, mp.b0, mp.b1, mp.b2, P,
