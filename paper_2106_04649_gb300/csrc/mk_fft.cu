@@ -371,19 +371,20 @@ __device__ __forceinline__ void pack_pair(const SurveyDev& s, float2* x, int t0,
 __device__ __forceinline__ int stage_ld(int nw) { return nw | 1; }
 
 // Resident epilogue CTAs per SM the launch is built for (registers and
-// shared memory are sized to fit that many).
-__host__ __device__ constexpr int epi_ctas(int nt) { return nt <= 2048 ? 2 : 1; }
-__host__ __device__ constexpr int epi_threads(int nt) { return threads_for(nt); }
+// shared memory are sized to fit that many, the grid holds that many per SM):
+// 16 warps per SM at every length; 256 threads per CTA from nt = 2048 up.
+__host__ __device__ constexpr int epi_ctas(int nt) { return nt <= 512 ? 8 : (nt <= 1024 ? 4 : (nt <= 4096 ? 2 : 1)); }
+__host__ __device__ constexpr int epi_threads(int nt) { return nt == 4096 ? 256 : threads_for(nt); }
 __host__ __device__ constexpr size_t epi_smem_target(int nt) {
-  return epi_ctas(nt) >= 4 ? 55 * 1024 : (epi_ctas(nt) >= 3 ? 73 * 1024 : 113 * 1024);
+  return (size_t)227 * 1024 / epi_ctas(nt) - 2 * 1024;
 }
 
 // The f1 window samples of a pair are prefetched into shared memory (2 NT
 // floats) up to NT = 4096; above that the shared memory is needed elsewhere.
-__host__ __device__ constexpr bool epi_prefetch(int nt) { return nt <= 4096; }
+__host__ __device__ constexpr bool epi_prefetch(int nt) { return nt <= 2048; }
 // Up to NT = 4096 the transforms ping-pong between two buffers (one barrier
 // per pass instead of two).
-__host__ __device__ constexpr bool epi_pingpong(int nt) { return nt <= 4096; }
+__host__ __device__ constexpr bool epi_pingpong(int nt) { return nt <= 2048; }
 __host__ __device__ constexpr size_t epi_base_bytes(int nt) {
   return ((epi_pingpong(nt) ? 2 : 1) * (size_t)padded(nt) + nt) * sizeof(float2) +
          (epi_prefetch(nt) ? 2 * (size_t)nt * sizeof(float) : 0);
