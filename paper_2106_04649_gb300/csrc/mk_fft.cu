@@ -286,49 +286,6 @@ __device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int f
   }
 }
 
-// Forward transform of the pair held in x (a + i b), unpacked into the band
-// spectra A_m, B_m for m < nw and written to Nw[m][t0], Nw[m][t0 + 1]
-// (complex FP32 R) or into the 16-bit embedding (tensor-core precisions).
-template <int NT, int THREADS>
-__device__ __forceinline__ void forward_band_pair(const SurveyDev& s, float2* x, const float2* tw,
-                                                  int t0, bool hasb) {
-  fft_smem<NT, THREADS, false>(x, tw);
-  for (int m = threadIdx.x; m < s.nw; m += THREADS) {
-    const float2 zm = x[P(m)];
-    const float2 zc = cconj(x[P((NT - m) & (NT - 1))]);
-    const float2 A = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
-    const float dx = zm.x - zc.x, dy = zm.y - zc.y;
-    const float2 B = hasb ? make_float2(0.5f * dy, -0.5f * dx) : make_float2(0.f, 0.f);
-    if (s.rprec == 0) {
-      const int fa = t0 / s.ns, ka = t0 - fa * s.ns;
-      float2* row = s.Nw + (int64_t)m * s.nw_stride;
-      row[(int64_t)fa * s.r_pad + ka] = A;
-      if (hasb) {
-        const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
-        row[(int64_t)fb * s.r_pad + kb] = B;
-      }
-    } else if (s.rprec >= 8) {
-      // time-domain R load: trace t = k * ns + r into the 16-bit R layout
-      const int fa = t0 / s.ns, ka = t0 - fa * s.ns;
-      store_r16(s, s.rprec - 8, (int64_t)m * s.nw_stride + (int64_t)fa * s.r_pad + ka, A);
-      if (hasb) {
-        const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
-        store_r16(s, s.rprec - 8, (int64_t)m * s.nw_stride + (int64_t)fb * s.r_pad + kb, B);
-      }
-    } else {
-      const int fa = t0 / s.ns, ka = t0 - fa * s.ns;
-      const int fb = (t0 + 1) / s.ns, kb = t0 + 1 - fb * s.ns;
-      if (s.rprec == 2) {
-        store_embedding<false>(s, m, fa, ka, A.x, A.y);
-        if (hasb) store_embedding<false>(s, m, fb, kb, B.x, B.y);
-      } else {
-        store_embedding<true>(s, m, fa, ka, A.x, A.y);
-        if (hasb) store_embedding<true>(s, m, fb, kb, B.x, B.y);
-      }
-    }
-  }
-}
-
 // Hermitian pack of the band spectra S[m][t0], S[m][t0 + 1] into
 // x = X + iY (bins outside the band zero; DC and Nyquist real).  All global
 // loads of a thread are issued before its shared-memory stores.
@@ -368,7 +325,7 @@ __device__ __forceinline__ void pack_pair(const SurveyDev& s, float2* x, int t0,
 // stage's leading dimension ld is odd, so both the per-frequency and the
 // per-trace accesses of the stage are free of bank conflicts.
 
-__device__ __forceinline__ int stage_ld(int nw) { return nw | 1; }
+__host__ __device__ __forceinline__ int stage_ld(int nw) { return nw | 1; }
 
 // Resident epilogue CTAs per SM the launch is built for (registers and
 // shared memory are sized to fit that many, the grid holds that many per SM):
@@ -429,6 +386,29 @@ __device__ __forceinline__ void unpack_band_stage(const SurveyDev& s, const floa
     const float2 zc = cconj(z[P((NT - m) & (NT - 1))]);
     ra[m] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y + zc.y));
     if (hasb) rb[m] = make_float2(0.5f * (zm.y - zc.y), -0.5f * (zm.x - zc.x));
+  }
+}
+
+// A block's band spectra from the trace-major stage (row c of trace tb + c)
+// to Nw, to the 16-bit field embedding, or (rprec >= 8, loading R from its
+// time traces) to the R layout, in one coalesced pass: thread column cc, bins
+// mc, mc + mstep, ...
+__device__ __forceinline__ void stage_store(const SurveyDev& s, const float2* stage, int ld, int tb, int ntr, int cc,
+                                            int mc, int mstep) {
+  if (cc >= ntr) return;
+  const int t = tb + cc;
+  const int f = t / s.ns, k = t - f * s.ns;
+  const float2* row = stage + cc * ld;
+  if (s.rprec == 0) {
+    float2* dst = s.Nw + (int64_t)f * s.r_pad + k;
+    for (int m = mc; m < s.nw; m += mstep) dst[(int64_t)m * s.nw_stride] = row[m];
+  } else if (s.rprec >= 8) {
+    const int64_t base = (int64_t)f * s.r_pad + k;
+    for (int m = mc; m < s.nw; m += mstep) store_r16(s, s.rprec - 8, (int64_t)m * s.nw_stride + base, row[m]);
+  } else if (s.rprec == 2) {
+    for (int m = mc; m < s.nw; m += mstep) store_embedding<false>(s, m, f, k, row[m].x, row[m].y);
+  } else {
+    for (int m = mc; m < s.nw; m += mstep) store_embedding<true>(s, m, f, k, row[m].x, row[m].y);
   }
 }
 
@@ -603,24 +583,7 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       s.Epart[tb + threadIdx.x] = e;
     }
     // 6. the block's new band spectra, one coalesced pass
-    if (cc < ntr) {
-      const int t = tb + cc;
-      const int f = t / s.ns, k = t - f * s.ns;
-      if (s.rprec == 0) {
-        float2* dst = s.Nw + (int64_t)f * s.r_pad + k;
-        for (int m = mc; m < s.nw; m += mstep) dst[(int64_t)m * s.nw_stride] = stage[cc * ld + m];
-      } else if (s.rprec == 2) {
-        for (int m = mc; m < s.nw; m += mstep) {
-          const float2 v = stage[cc * ld + m];
-          store_embedding<false>(s, m, f, k, v.x, v.y);
-        }
-      } else {
-        for (int m = mc; m < s.nw; m += mstep) {
-          const float2 v = stage[cc * ld + m];
-          store_embedding<true>(s, m, f, k, v.x, v.y);
-        }
-      }
-    }
+    stage_store(s, stage, ld, tb, ntr, cc, mc, mstep);
     __syncthreads();
   }
 
@@ -649,40 +612,63 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   }
 }
 
-template <int NT>
+// Band spectra of a field, in blocks of 2G consecutive traces: per pair a
+// forward transform in shared memory, the band into the block's stage, then
+// one coalesced pass out (stage_store).  MODE 0: the spectrum of a field
+// src [F][ns][nt] (Nw or its embedding; R when loading R from time traces).
+// MODE 1: the initialisation N_{-1} = f1plus = G_d(-t), f1min = 0 from
+// src = G_d, and the spectrum of N_{-1}.
+template <int NT, int MODE>
 __global__ void __launch_bounds__(threads_for(NT))
-init_kernel(SurveyDev s, const float* __restrict__ Gd) {
+band_kernel(SurveyDev s, const float* __restrict__ src, int G) {
   constexpr int THREADS = threads_for(NT);
   constexpr int PJ = NT / THREADS;
   extern __shared__ float4 smem_raw[];
   float2* x = reinterpret_cast<float2*>(smem_raw);
   float2* tw = x + padded(NT);
+  float2* stage = tw + NT;  // [2G][ld]
+  const int ld = stage_ld(s.nw);
   for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
   __syncthreads();
-  const int npairs = (s.ncols + 1) / 2;
-  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
-    const int t0 = 2 * p;
-    const bool hasb = t0 + 1 < s.ncols;
-    const int64_t ba = field_offset(s, t0);
-    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+  const int bt = 2 * G;
+  const int nblocks = (s.ncols + bt - 1) / bt;
+  const int cc = threadIdx.x & (bt - 1);
+  const int mc = threadIdx.x / bt, mstep = THREADS / bt;
+  for (int blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    const int tb = blk * bt;
+    const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
+    for (int q = 0; 2 * q < ntr; ++q) {
+      const int t0 = tb + 2 * q;
+      const bool hasb = 2 * q + 1 < ntr;
+      const int64_t ba = field_offset(s, t0);
+      const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
+      if constexpr (MODE == 1) {
 #pragma unroll
-    for (int q = 0; q < PJ; ++q) {
-      const int j = threadIdx.x + q * THREADS;
-      const int jr = (NT - j) & (NT - 1);
-      const float na = Gd[ba + jr];  // G_d has the field layout [F][nrec][nt]
-      const float nb = hasb ? Gd[bb + jr] : 0.f;
-      x[P(j)] = make_float2(na, nb);
-      s.fN[ba + j] = na;
-      s.f1p[ba + j] = na;
-      s.f1m[ba + j] = 0.f;
-      if (hasb) {
-        s.fN[bb + j] = nb;
-        s.f1p[bb + j] = nb;
-        s.f1m[bb + j] = 0.f;
+        for (int u = 0; u < PJ; ++u) {
+          const int j = threadIdx.x + u * THREADS;
+          const int jr = (NT - j) & (NT - 1);
+          const float na = src[ba + jr];  // G_d has the field layout [F][nrec][nt]
+          const float nb = hasb ? src[bb + jr] : 0.f;
+          x[P(j)] = make_float2(na, nb);
+          s.fN[ba + j] = na;
+          s.f1p[ba + j] = na;
+          s.f1m[ba + j] = 0.f;
+          if (hasb) {
+            s.fN[bb + j] = nb;
+            s.f1p[bb + j] = nb;
+            s.f1m[bb + j] = 0.f;
+          }
+        }
+      } else {
+        for (int j = threadIdx.x; j < NT; j += THREADS)
+          x[P(j)] = make_float2(src[ba + j], hasb ? src[bb + j] : 0.f);
       }
+      __syncthreads();
+      fft_smem<NT, THREADS, false>(x, tw);
+      unpack_band_stage<NT, THREADS>(s, x, stage + (2 * q) * ld, stage + (2 * q + 1) * ld, hasb);
+      __syncthreads();
     }
-    __syncthreads();
-    forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
+    stage_store(s, stage, ld, tb, ntr, cc, mc, mstep);
     __syncthreads();
   }
 }
@@ -705,30 +691,6 @@ __global__ void window_kernel(SurveyDev s, const double* __restrict__ td, double
     L = (int)(Lq > s.nt / 2 + 1 ? s.nt / 2 + 1 : Lq);
   }
   s.L[t] = L;
-}
-
-// Band spectrum (Nw or its 16-bit embedding) of a field [F][ns][nt].
-template <int NT>
-__global__ void __launch_bounds__(threads_for(NT))
-spectrum_kernel(SurveyDev s, const float* __restrict__ src) {
-  constexpr int THREADS = threads_for(NT);
-  extern __shared__ float4 smem_raw[];
-  float2* x = reinterpret_cast<float2*>(smem_raw);
-  float2* tw = x + padded(NT);
-  for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
-  __syncthreads();
-  const int npairs = (s.ncols + 1) / 2;
-  for (int p = blockIdx.x; p < npairs; p += gridDim.x) {
-    const int t0 = 2 * p;
-    const bool hasb = t0 + 1 < s.ncols;
-    const int64_t ba = field_offset(s, t0);
-    const int64_t bb = hasb ? field_offset(s, t0 + 1) : 0;
-    for (int j = threadIdx.x; j < NT; j += THREADS)
-      x[P(j)] = make_float2(src[ba + j], hasb ? src[bb + j] : 0.f);
-    __syncthreads();
-    forward_band_pair<NT, THREADS>(s, x, tw, t0, hasb);
-    __syncthreads();
-  }
 }
 
 // Inverse transform of the band spectra in S, per trace:
@@ -846,9 +808,9 @@ cudaError_t set_attrs() {
   // the epilogue's stage grows with the band: allow the per-CTA maximum
   cudaError_t e = cudaFuncSetAttribute(epilogue_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEpiSmemMax);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(init_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
+  e = cudaFuncSetAttribute(band_kernel<NT, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEpiSmemMax);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(spectrum_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
+  e = cudaFuncSetAttribute(band_kernel<NT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kEpiSmemMax);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(inverse_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, one);
 }
@@ -862,12 +824,19 @@ cudaError_t launch_inv_nt(const SurveyDev& s, float* dst, int mode, cudaStream_t
   return cudaGetLastError();
 }
 
-template <int NT>
-cudaError_t launch_spec_nt(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms) {
-  const int npairs = (s.ncols + 1) / 2;
-  int grid = num_sms * 4;
-  if (grid > npairs) grid = npairs;
-  spectrum_kernel<NT><<<grid, threads_for(NT), (padded(NT) + NT) * sizeof(float2), st>>>(s, src);
+// Blocks of the band kernels: up to 4 pairs while two CTAs fit per SM, fewer
+// when there are few traces, so that every SM gets work.
+template <int NT, int MODE>
+cudaError_t launch_band_nt(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms) {
+  const size_t base = ((size_t)padded(NT) + NT) * sizeof(float2);
+  const size_t row = (size_t)stage_ld(s.nw) * sizeof(float2);
+  int G = 4;
+  while (G > 1 && (base + 2 * G * row > 113 * 1024 || (s.ncols + 2 * G - 1) / (2 * G) < 2 * num_sms)) G /= 2;
+  const size_t bytes = base + 2 * (size_t)G * row;
+  const int nblocks = (s.ncols + 2 * G - 1) / (2 * G);
+  int grid = num_sms * 2;
+  if (grid > nblocks) grid = nblocks;
+  band_kernel<NT, MODE><<<grid, threads_for(NT), bytes, st>>>(s, src, G);
   return cudaGetLastError();
 }
 
@@ -901,15 +870,7 @@ cudaError_t launch_epi_nt(const SurveyDev& s, double* ring, int slots, cudaStrea
   return cudaGetLastError();
 }
 
-template <int NT>
-cudaError_t launch_init_nt(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms) {
-  const int npairs = (s.ncols + 1) / 2;
-  int grid = num_sms * 4;
-  if (grid > npairs) grid = npairs;
-  const size_t bytes = (padded(NT) + NT) * sizeof(float2);
-  init_kernel<NT><<<grid, threads_for(NT), bytes, st>>>(s, Gd);
-  return cudaGetLastError();
-}
+
 
 }  // namespace
 
@@ -976,7 +937,7 @@ cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStr
 }
 
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms) {
-#define MK_CALL(N) launch_init_nt<N>(s, Gd, st, num_sms)
+#define MK_CALL(N) launch_band_nt<N, 1>(s, Gd, st, num_sms)
   MK_NT_SWITCH(s.nt, MK_CALL)
 #undef MK_CALL
 }
@@ -987,7 +948,7 @@ cudaError_t launch_windows(const SurveyDev& s, const double* td, double eps, cud
 }
 
 cudaError_t launch_spectrum(const SurveyDev& s, const float* src, cudaStream_t st, int num_sms) {
-#define MK_CALL(N) launch_spec_nt<N>(s, src, st, num_sms)
+#define MK_CALL(N) launch_band_nt<N, 0>(s, src, st, num_sms)
   MK_NT_SWITCH(s.nt, MK_CALL)
 #undef MK_CALL
 }
