@@ -500,6 +500,16 @@ def main_ours(args):
             d = summarize(vs, vf, vp, vms, vsteps, vst)
             d.update({"nfocal": vf, "rprec": vp, "steps": vsteps})
             variants.append(d)
+        # the headline workload replayed as one CUDA graph per iteration, without the
+        # per-launch timing events of the headline run
+        gs = survey(1)
+        grn = Runner([(gs, "c64")], dev, local, R_dev=R_dev, timing=False, graph=True)
+        gms, gst, _ = grn.timed(200, 5)
+        grn.close()
+        variants.append({"workload": "paper-small F=1, complex FP32, iterations replayed as a CUDA graph "
+                                     "(no per-launch timing events)", "nfocal": 1,
+                         "value": 200 / (gms / 1e3), "ms_per_step": gms / 200,
+                         "gpu_launches_per_step": gst["launches"] / 200})
         # out-of-core R: the band streamed from pinned host memory every contraction
         for vf in (1, 64):
             vs = survey(vf)
