@@ -39,6 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NITER = 16
+TIMING_STRIDE = 4  # time the kernels of every 4th iteration (events between launches cost ~4%)
 L2_NOTE = "inputs larger than L2: R (0.71-2.1 GB) is streamed from HBM every iteration"
 RPREC = {"c64": 0, "cbf16": 1, "cf16": 2, "split": 3, "split3": 4}
 NPROD = {1: 2, 2: 2, 3: 3, 4: 6}  # tensor-core products per complex MAC, per 16-bit form
@@ -302,6 +303,7 @@ class Runner:
         from paper_2106_04649_gb300.api import Desc, Plan
         from paper_2106_04649_gb300 import _native as N
         self.items = items
+        self.timing = timing
         flags = (N.MK_FLAG_TIMING if timing else 0) | (N.MK_FLAG_GRAPH if graph else 0)
         flags |= N.MK_FLAG_STREAM_R if stream_r else 0
         descs = [Desc(s.n, s.n, s.nt, s.nfocal, s.dt, s.dx, s.fmax_hz or 0.0, RPREC[rp], flags) for s, rp in items]
@@ -337,6 +339,12 @@ class Runner:
 
     def timed(self, steps, warmup, clocks=None, dist=None):
         import torch
+        from paper_2106_04649_gb300 import binding as B
+        if self.timing:
+            # kernel durations from the events around the launches of every TIMING_STRIDE-th
+            # iteration, with every event pair created before the timed region
+            reserve = ((warmup + steps) * NITER // TIMING_STRIDE + 2) * 2 * len(self.items)
+            B.mk_set_timing(self.plan.handle, TIMING_STRIDE, reserve)
         for _ in range(warmup):
             self.step()
         torch.cuda.synchronize()
@@ -374,7 +382,9 @@ def summarize(s, F, rprec, ms, steps, st, world=1):
         "synthesis": {"algorithmic_tflops": flops / (c_ms * 1e-3) / 1e12,
                       "hbm_gbs_R": s.nw * s.n * s.n * RBYTES[rprec] / (c_ms * 1e-3) / 1e9,
                       "contract_ms": c_ms, "epilogue_ms": e_ms,
-                      "share_contract": st["contract_ms"] / max(1e-9, ms)},
+                      "timed_launches": {"contraction": int(st["contract_timed"]),
+                                         "epilogue": int(st["epilogue_timed"])},
+                      "share_contract": c_ms * st["contract_launches"] / max(1e-9, ms)},
         "gpu_launches": int(st["launches"]),
     }
 
@@ -424,6 +434,7 @@ def main_ours(args):
         energy = torch.empty((NITER, F), dtype=torch.float64).pin_memory()
         h2d = Rh.numel() * 8 + Gd_h.nbytes + td_h.nbytes
         d2h = Gout.numel() * 4 + energy.numel() * 8
+        B.mk_set_timing(run.plan.handle, 1 << 30, 0)  # no per-launch events in the end-to-end runs
         s2 = torch.cuda.Stream(dev)
         other = Plan([Desc(s.n, s.n, s.nt, F, s.dt, s.dx, s.fmax_hz or 0.0, RPREC[args.rprec], 0)],
                      device=local, stream=s2)
@@ -534,11 +545,14 @@ def main_ours(args):
         # aggregate roofline: each survey's contraction roof (its own bound), summed, over the
         # summed measured contraction time
         roof_ms = NITER * sum(lower_bound_ms(x, x.nfocal, rp)[1] for x, rp in items)
+        # per-step totals: the timed launches are a sample of every iteration's launches
+        c_step = bst["contract_ms"] * bst["contract_launches"] / max(1, bst["contract_timed"]) / 5
+        e_step = bst["epilogue_ms"] * bst["epilogue_launches"] / max(1, bst["epilogue_timed"]) / 5
         variants.append({"workload": "batching: 12 surveys, n 201-1201, nt 1024-4096, 1-256 focal points, "
                                      "even surveys c64, odd surveys split3, one plan, stream launches", "nfocal": br.F,
                          "value": br.F * 5 / (bms / 1e3), "ms_per_step": bms / 5,
-                         "contract_ms_total": bst["contract_ms"] / 5, "epilogue_ms_total": bst["epilogue_ms"] / 5,
-                         "contraction_roofline_frac": roof_ms / (bst["contract_ms"] / 5),
+                         "contract_ms_total": c_step, "epilogue_ms_total": e_step,
+                         "contraction_roofline_frac": roof_ms / c_step,
                          "contraction_bounds": {b: sum(1 for x, rp in items if lower_bound_ms(x, x.nfocal, rp)[0] == b)
                                                 for b in ("hbm", "alu", "tensor")},
                          "gpu_launches_per_step": bst["launches"] / 5})

@@ -341,6 +341,17 @@ mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float* Gd, const
                          int32_t niter, float* fields, double* energy, void* cuda_stream);
 
 /*
+ * mk_set_timing - for a plan made with MK_FLAG_TIMING: record the CUDA
+ * events around the contraction and epilogue launches of every stride-th
+ * iteration only (1 = every iteration, the default), counted from this call,
+ * and create reserve_pairs event pairs now, so that timed launches create
+ * none.  mk_get_stats then averages over the timed launches.
+ * Errors: MK_ERR_ARG (stride < 1, reserve < 0), MK_ERR_STATE (no
+ * MK_FLAG_TIMING), MK_ERR_CUDA.
+ */
+mk_status mk_set_timing(mk_plan_t plan, int32_t stride, int32_t reserve_pairs);
+
+/*
  * Tuning of one survey's kernels (MK_FLAG_AUTOTUNE).  Candidates: the N tile
  * of the tensor-core contraction (16, 32, 64 or 128 columns of the real
  * field embedding, up to the first power of two covering 2 nfocal) and the

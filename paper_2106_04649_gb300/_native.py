@@ -82,6 +82,7 @@ _SIGS = {
     "mk_attach_R_host": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t]),
     "mk_load_R_time": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "mk_get_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(MkTuning)]),
+    "mk_set_timing": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,
                                       _P]),
 }

@@ -52,6 +52,10 @@ def mk_load_R(plan: int, survey: int, Rw: int, w_begin: int, w_count: int, src_o
     _check(N.load().mk_load_R(plan, survey, Rw, w_begin, w_count, int(src_on_device)), plan)
 
 
+def mk_set_timing(plan: int, stride: int, reserve_pairs: int) -> None:
+    _check(N.load().mk_set_timing(plan, stride, reserve_pairs), plan)
+
+
 def mk_get_tuning(plan: int, survey: int) -> dict:
     t = N.MkTuning()
     _check(N.load().mk_get_tuning(plan, survey, ctypes.byref(t)), plan)

@@ -60,6 +60,8 @@ struct mk_plan_s {
   int device = 0;
   int num_sms = 1;
   bool timing = false;
+  int timing_stride = 1;        // time the launches of every timing_stride-th iteration
+  unsigned long long timing_count = 0;  // iterations launched with timing on
   char err[512] = "";
   mk_stats_t stats{};
   std::vector<TimedPair> events;  // created once, reused
@@ -917,7 +919,8 @@ extern "C" mk_status mk_iterate(mk_plan_t p, int32_t niter, double* energy) {
     for (int it = 0; it < chunk; ++it) {
       if (use_graph) {
         MK_CUDA(p, cudaGraphLaunch(p->graph_exec, p->stream));
-      } else if ((st = launch_iteration(p, p->timing, p->stream, false)) != MK_OK) {
+      } else if ((st = launch_iteration(p, p->timing && (p->timing_count++ % (unsigned long long)p->timing_stride) == 0,
+                                        p->stream, false)) != MK_OK) {
         return st;
       }
     }
@@ -1048,6 +1051,28 @@ mk_status mk_image(mk_plan_t p, int32_t survey, double* image, int32_t dst_on_de
     MK_CUDA(p, cudaMemcpyAsync(image, dst, (size_t)v.F * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     MK_CUDA(p, cudaStreamSynchronize(p->stream));
     if ((st = check_device_errors(p)) != MK_OK) return st;
+  }
+  return MK_OK;
+}
+
+mk_status mk_set_timing(mk_plan_t p, int32_t stride, int32_t reserve_pairs) {
+  if (!p) return fail(nullptr, MK_ERR_ARG, "null plan");
+  p->err[0] = 0;
+  if (stride < 1 || reserve_pairs < 0) return fail(p, MK_ERR_ARG, "stride must be >= 1 and reserve >= 0");
+  if (!p->timing) return fail(p, MK_ERR_STATE, "the plan was made without MK_FLAG_TIMING");
+  mk_status st = ensure_device(p);
+  if (st != MK_OK) return st;
+  p->timing_stride = stride;
+  p->timing_count = 0;
+  while (p->events.size() < p->next_event + (size_t)reserve_pairs) {
+    TimedPair tp;
+    MK_CUDA(p, cudaEventCreate(&tp.a));
+    if (cudaEventCreate(&tp.b) != cudaSuccess) {
+      cudaEventDestroy(tp.a);
+      return fail(p, MK_ERR_CUDA, "cudaEventCreate failed");
+    }
+    tp.kind = 0;
+    p->events.push_back(tp);
   }
   return MK_OK;
 }
