@@ -430,8 +430,11 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   __shared__ int sL[8];                // window half-lengths of the block's traces
   __shared__ int s_last;
 
-  for (int i = threadIdx.x; i < NT; i += THREADS) tw[i] = s.tw[i];
-  __syncthreads();
+  // the twiddle table arrives asynchronously while the first block's spectra
+  // load; the wait sits before the block's first barrier
+  for (int i = 2 * threadIdx.x; i < NT; i += 2 * THREADS)
+    cp_async16(reinterpret_cast<float*>(tw + i), reinterpret_cast<const float*>(s.tw + i));
+  cp_async_commit();
 
   // the iteration index lives on the device (the last CTA advances it), so
   // every iteration launches with identical arguments (graph replay)
@@ -463,6 +466,7 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       for (; m < s.nw; m += mstep) dst[m] = __ldg(src + (int64_t)m * s.s_stride);
     }
     if (threadIdx.x < ntr) sL[threadIdx.x] = s.L[tb + threadIdx.x];  // the block's window lengths
+    cp_async_wait_all();  // the twiddle table (first block)
     __syncthreads();
     for (int q = 0; 2 * q < ntr; ++q) {
       const int t0 = tb + 2 * q;
