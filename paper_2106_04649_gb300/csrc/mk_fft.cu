@@ -430,6 +430,10 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
   __shared__ int sL[8];                // window half-lengths of the block's traces
   __shared__ int s_last;
 
+  // a kernel launched as a programmatic dependent of this one (the next
+  // contraction) may be scheduled now; it waits for this grid to complete
+  // before it reads what this grid writes
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // the twiddle table arrives asynchronously while the first block's spectra
   // load; the wait sits before the block's first barrier
   for (int i = 2 * threadIdx.x; i < NT; i += 2 * THREADS)

@@ -168,9 +168,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 
 constexpr int kUnitRows = 64;  // rows per work unit, all of one frequency (8 stages of 8 rows)
 
-// Work is handed out dynamically: the producer lane takes units of up to 64
-// rows of one frequency from a global counter, so SMs that stream faster take
-// more units and all finish together.  A stage records its first row and row
+// Work is handed out dynamically: after its first unit (unit blockIdx.x) the
+// producer lane takes units of up to 64 rows of one frequency from a global
+// counter, so SMs that stream faster take more units and all finish together.  A stage records its first row and row
 // count; a stage without rows ends the stream.  The last CTA to finish
 // resets the counters (queue[0]: next unit, queue[1]: finished CTAs), so
 // every launch starts from zero; no thread leaves before the final barrier.
@@ -201,8 +201,10 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
     if (lane == 0) {
       bool ok = true;
       uint32_t it = 0;
-      for (;;) {
-        const int u = (int)atomicAdd(queue, 1u);
+      // the first unit is this CTA's own (its rows of R can stream before the
+      // previous kernel has finished); the counter hands out the rest, after
+      // the wait for the previous grid (which may be a GEMV still using it)
+      for (int u = blockIdx.x;; u = (int)gridDim.x + (int)atomicAdd(queue, 1u)) {
         if (u >= nunits) break;
         const int m = u / upf;
         const int k0 = (u - m * upf) * kUnitRows;
@@ -222,6 +224,7 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
           bulk_g2s(smem_u32(ring + (size_t)s * stage_f4), R + row * rq, bytes, smem_u32(&full_bar[s]));
         }
         if (!ok) break;
+        if (u == (int)blockIdx.x) asm volatile("griddepcontrol.wait;" ::: "memory");
       }
       if (ok) {  // end of the stream: a stage without rows
         const int s = (int)(it % stages);
@@ -241,7 +244,11 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
       if (!ok && err) atomicExch(err, 1);
     }
   } else {
-    // consumers: warp w reduces row w of every stage
+    // consumers: warp w reduces row w of every stage.  When launched as a
+    // programmatic dependent of the previous kernel (the epilogue that writes
+    // Nw and reads S), wait for that grid here: the producer's copies of R
+    // may already be under way.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int cur_w = -1;
     float4 nv[PER];
     for (uint32_t it = 0;; ++it) {
@@ -314,11 +321,22 @@ cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   const int stages = bulk_stages(rq);
   const size_t smem = (size_t)stages * kConsWarps * rq * 16;
   const int64_t units = (int64_t)s.nw * ((s.ns + kUnitRows - 1) / kUnitRows);
-  const int64_t grid = units < num_sms ? units : num_sms;
-  gemv_bulk_kernel<PER><<<(unsigned)grid, kBulkThreads, smem, st>>>(
-      reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq,
-      s.nw_stride / 2, s.s_stride, s.c, s.nw, stages, s.counter + 1, s.err);
-  return cudaGetLastError();
+  const int64_t grid = units < num_sms ? units : num_sms;  // every CTA has a first unit
+  // programmatic dependent launch: the CTAs may start on SMs the previous
+  // kernel has left while its last CTAs finish
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBulkThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, gemv_bulk_kernel<PER>, reinterpret_cast<const float4*>(s.R),
+                            reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq, s.nw_stride / 2, s.s_stride, s.c,
+                            s.nw, stages, s.counter + 1, s.err);
 }
 
 template <int PER>
