@@ -267,7 +267,9 @@ def main_reference(args):
     if rank != 0:
         return
     s = survey(args.nfocal)
-    reps = args.warmup + args.steps
+    # a bounded sample, so that the run ends within minutes whatever --steps asks for:
+    # at most 120 repetitions of one focal point (~1 minute on 16 cores), or 3 + a few of a line
+    reps = min(args.warmup + args.steps, 120)
     if args.nfocal > 1:
         reps = min(reps, 3 + max(1, args.warmup // 5))
     out, cores, sample = run_cpu_oracle(args.nfocal, reps)
