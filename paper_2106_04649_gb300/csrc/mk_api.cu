@@ -133,7 +133,11 @@ size_t layout(Survey& sv, char* base) {
   v.nt = d.nt;
   v.F = d.nfocal;
   v.nw = band_bins(d);
-  v.r_pad = (d.nrec + 31) / 32 * 32;
+  // rows of R padded for aligned loads: to 32 complex values for the tensor-core and
+  // SIMT GEMM tiles and for the host layout of streamed R; a GEMV-only survey (complex
+  // FP32, one focal point, resident R) needs 16-byte rows only, an even count
+  const bool gemv_only = d.rprec == MK_R_C64 && d.nfocal == 1 && !(d.flags & MK_FLAG_STREAM_R);
+  v.r_pad = gemv_only ? (d.nrec + 1) / 2 * 2 : (d.nrec + 31) / 32 * 32;
   v.ncols = v.ns * v.F;
   v.s_stride = ((int64_t)v.ncols + 1 + 3) / 4 * 4;
   v.nw_stride = (int64_t)v.r_pad * v.F;
