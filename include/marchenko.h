@@ -77,7 +77,7 @@ typedef enum {
   MK_ERR_OOM = 3,          /* workspace too small                            */
   MK_ERR_CUDA = 4,         /* a CUDA runtime call failed                     */
   MK_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out             */
-  MK_ERR_UNSUPPORTED = 6   /* valid request this build does not implement    */
+  MK_ERR_UNSUPPORTED = 6   /* valid request the library does not support      */
 } mk_status;
 
 /* Storage precision of R in the workspace. */

@@ -653,7 +653,7 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
       p->stats.launches++;
       p->stats.other_launches++;
     } else {
-      // pageable host memory: the driver stages the copy
+      // pageable host memory: the CUDA driver stages the copy
       MK_CUDA(p, cudaMemcpy2DAsync(dst, (size_t)v.r_pad * sizeof(float2), Rw, (size_t)v.ns * sizeof(float2),
                                    (size_t)v.ns * sizeof(float2), (size_t)rows, cudaMemcpyHostToDevice,
                                    p->stream));
