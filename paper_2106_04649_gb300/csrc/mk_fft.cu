@@ -23,11 +23,14 @@
 // transform of X + iY with Hermitian X, Y gives x + iy; the forward transform
 // Z of a + ib gives A_m = (Z_m + conj Z_{-m})/2, B_m = (Z_m - conj Z_{-m})/(2i).
 // The complex transform is a Stockham autosort FFT in shared memory with
-// twiddles from an FP64 host
-// table rounded to FP32 (radix-8 passes, contiguous per-pass twiddle tables
-// and a padded shared-memory index keep the accesses bank-conflict free).
-// One CTA processes one pair of traces at a time and loops over pairs
-// (grid sized to the SM count).
+// twiddles from an FP64 host table rounded to FP32 (radix-8 passes,
+// contiguous per-pass twiddle tables and a padded shared-memory index keep
+// the accesses bank-conflict free).  The epilogue and the band kernel
+// (initialisation, field spectra) take blocks of up to 8 consecutive traces:
+// the blocks' band spectra pass through a trace-major shared stage, so that
+// the loads from S and the stores to Nw or the 16-bit embedding are
+// coalesced; the pairs of a block are transformed one after the other.
+// Grids are sized to the SM count times the CTAs that fit per SM.
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
