@@ -27,6 +27,12 @@
 //                  signals the epilogue;
 //  warps 2..5    : epilogue, one TMEM lane (= output row) per thread:
 //                  tcgen05.ld -> scale by c -> complex stores to S.
+// Tiles (frequency, 128-row block, N block; N block fastest, so that
+// neighbouring CTAs share an R tile through L2) come from a global work
+// counter: the producer takes each tile index and passes it to the MMA lane
+// and the epilogue warps through a small mbarrier-guarded queue in shared
+// memory; a tile index of -1 ends the work, and the last CTA to finish
+// resets the counter.
 // Accuracy: the tensor core's FP32 accumulation over a long K chain carries
 // a rounding bias that, on cancelling sums, dominates the operand precision
 // of the split forms.  With PROMOTE the MMAs of each 64-wide K block start a
