@@ -359,8 +359,8 @@ mk_status mk_set_timing(mk_plan_t plan, int32_t stride, int32_t reserve_pairs);
  * candidate runs once untimed and three times timed with CUDA events on the
  * plan's stream, on the survey's own buffers, before the fields are
  * initialised; the fastest is kept.  Choices are cached per process, keyed by
- * (nsrc, nt, n_w, nfocal, rprec), so later plans of the same shape skip the
- * timing.  Results do not depend on the choice.
+ * (nsrc, nt, n_w, nfocal, rprec) and the device's SM count, so later plans of
+ * the same shape skip the timing.  Results do not depend on the choice.
  */
 typedef struct {
   int32_t tuned;        /* 0: heuristic choice, 1: timed now, 2: taken from the cache */

@@ -322,19 +322,19 @@ mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch) {
 }
 
 // Tuning (MK_FLAG_AUTOTUNE): per-process cache of the fastest kernel shapes,
-// keyed by (nsrc, nt, n_w, nfocal, rprec).
+// keyed by (nsrc, nt, n_w, nfocal, rprec) and the device's SM count.
 struct TuneChoice {
   int bn, g;
   float contract_ms, epilogue_ms;
 };
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int>, TuneChoice> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int>, TuneChoice> g_tune_cache;
 
 // Times each candidate shape of the survey's contraction and epilogue on its
 // own buffers (the fields are initialised afterwards) and keeps the fastest.
 mk_status tune_survey(mk_plan_t p, Survey& sv) {
   mk::SurveyDev& v = sv.dev;
-  const auto key = std::make_tuple(v.ns, v.nt, v.nw, v.F, v.rprec);
+  const auto key = std::make_tuple(v.ns, v.nt, v.nw, v.F, v.rprec, p->num_sms);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
