@@ -348,7 +348,10 @@ mk_status tune_survey(mk_plan_t p, Survey& sv) {
   }
   cudaEvent_t e0, e1;
   MK_CUDA(p, cudaEventCreate(&e0));
-  MK_CUDA(p, cudaEventCreate(&e1));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(p, MK_ERR_CUDA, "cudaEventCreate failed");
+  }
   int candidates = 0;
   mk_status result = MK_OK;
   // best of three timed runs after one untimed run
