@@ -85,3 +85,24 @@ def test_null_arguments_rejected_without_gpu():
     assert lib.mk_load_R(None, 0, None, 0, 0, 0) == N.MK_ERR_ARG
     assert lib.mk_destroy(None) == N.MK_OK
     assert b"null" in lib.mk_last_error(None)
+
+
+def test_python_constants_match_header():
+    """Every MK_ constant the binding defines has the header's value."""
+    from paper_2106_04649_gb300 import _native as N
+    text = open(HEADER).read()
+    values = {}
+    for name, expr in re.findall(r"#define\s+(MK_[A-Z0-9_]+)\s+\(?([^/\n]+?)\)?\s*(?:/\*|\n)", text):
+        expr = expr.replace("u <<", " <<").replace("u)", ")").replace("0xFFu", "0xFF").strip().rstrip("u")
+        try:
+            values[name] = eval(expr, {"size_t": int})
+        except Exception:
+            pass
+    for name, val in re.findall(r"\b(MK_(?:R|OK|ERR)_?[A-Z0-9_]*)\s*=\s*(\d+)", text):
+        values[name] = int(val)
+    checked = 0
+    for name, val in values.items():
+        if hasattr(N, name):
+            assert getattr(N, name) == val, name
+            checked += 1
+    assert checked >= 20
