@@ -180,7 +180,10 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
  *       call returns once the copy is queued, MK_ERR_ARG if the memory is
  *       not page-locked).
  * Loading may be done in chunks of bins, in any order; mk_set_Gd_window
- * requires every bin 0 .. n_w-1 to have been loaded.
+ * requires every bin 0 .. n_w-1 to have been loaded.  Loading R after
+ * mk_set_Gd_window keeps the state of the series: the next mk_iterate
+ * continues from it with the new R, and pmin (hence G) is formed at fetch
+ * with the R loaded at that time (pmin = synthesis of f2p - N_last).
  * Errors: MK_ERR_ARG (bad survey index or bin range), MK_ERR_CUDA.
  */
 mk_status mk_load_R(mk_plan_t plan, int32_t survey, const void* Rw, int32_t w_begin,
@@ -250,6 +253,10 @@ mk_status mk_iterate(mk_plan_t plan, int32_t niter, double* energy);
  * f1min only; N_last, f2p, pmin and G are formed on the GPU when fetched
  * (f2p = f1plus - f1min(-t); pmin = synthesis of f2p - N_last, one extra
  * contraction; G = f2p(-t) + pmin), which is exact algebra of Algorithm 1.
+ * A resident complex FP32 survey with one focal point instead accumulates
+ * pmin during the iterations as it stands in Algorithm 1, as the sum of the
+ * synthesis results' band spectra, and forms it at fetch with one inverse
+ * transform (no extra contraction).
  * MK_F_GMINUS is the up-going Green's function of Algorithm 1 (one extra
  * synthesis of f1plus after the loop, minus f1min); MK_F_GPLUS the
  * down-going one, f1plus(-t) minus the synthesis of f1min(-t) (Theory: each
@@ -326,7 +333,9 @@ mk_status mk_get_stats(mk_plan_t plan, mk_stats_t* out, int32_t reset);
  *
  *   d:      one survey (rprec must be MK_R_C64).
  *   R:      device, complex64 [n_w][nsrc][r_pad], r_pad = nrec rounded up to
- *           a multiple of 32, padding entries zero (the plan's R layout).
+ *           a multiple of 32, padding entries zero.  (A plan for a single
+ *           focal point pads its own R rows only to an even count; this entry
+ *           point always takes rows padded to 32.)
  *   Gd, td: device, as for mk_set_Gd_window.
  *   niter:  iterations (>= 0).
  *   fields: device float [5][nfocal][nsrc][nt]: N, f1plus, f1min, f2p, pmin
@@ -334,7 +343,10 @@ mk_status mk_get_stats(mk_plan_t plan, mk_stats_t* out, int32_t reset);
  *   energy: device double [niter][nfocal], or NULL.
  *   cuda_stream: stream for all the work; the call returns without waiting.
  * Errors (message via mk_last_error(NULL)): MK_ERR_ARG, MK_ERR_UNSUPPORTED,
- *         MK_ERR_CUDA.
+ *         MK_ERR_CUDA.  A bounded device wait that runs out (MK_ERR_TIMEOUT in
+ *         the plan entry points) cannot be returned by a call that does not
+ *         wait: the last kernel of the call then fills fields (and energy)
+ *         with NaN instead.
  */
 #define MK_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float* Gd, const double* td, double eps_s,

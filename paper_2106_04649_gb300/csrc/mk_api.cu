@@ -36,6 +36,11 @@ struct Survey {
   bool n_in_field = true;   // fN holds the last N (else it follows from S)
   bool derived_valid = false;  // f2p and pmin formed since the last change
   bool gm_valid = false, gp_valid = false;  // G^- and G^+ formed since the last change
+  // R was written (mk_load_R, mk_load_R_time) since the last contraction launch:
+  // the next contraction must not start as a programmatic dependent
+  bool r_written = true;
+  float2* pacc = nullptr;   // band spectrum of pmin, accumulated by the iterations (F = 1 surveys)
+  bool pacc_valid = false;  // pacc holds the spectrum of pmin of the current series
   size_t offset = 0, bytes = 0;  // carving inside the workspace
   // streaming of R from pinned host memory (MK_FLAG_STREAM_R)
   bool stream_r = false;
@@ -146,6 +151,8 @@ size_t layout(Survey& sv, char* base) {
   v.inv_nt = 1.0f / (float)d.nt;
   v.rprec = d.rprec;
   v.epi_g = 0;
+  v.pdl = 0;
+  v.pacc = nullptr;
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
     char* ptr = base ? base + off : nullptr;
@@ -187,6 +194,10 @@ size_t layout(Survey& sv, char* base) {
     v.Bq2 = d.rprec == MK_R_SPLIT3_BF16 ? take(bq) : nullptr;
   }
   v.S = reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)));
+  // a survey contracted by the GEMV accumulates pmin as a band spectrum during the
+  // iterations (Algorithm 1 adds every synthesis result to pmin): n_w * ns complex
+  // values, far less than R, and no extra contraction when pmin or G is fetched
+  sv.pacc = gemv_only ? reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2))) : nullptr;
   v.fN = reinterpret_cast<float*>(take(field));
   v.f1p = reinterpret_cast<float*>(take(field));
   v.f1m = reinterpret_cast<float*>(take(field));
@@ -204,29 +215,6 @@ size_t layout(Survey& sv, char* base) {
   v.tw = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));
   sv.energy = reinterpret_cast<double*>(take((size_t)kMaxIterSlots * v.F * sizeof(double)));
   return off;
-}
-
-// Twiddles of the shared-memory FFT (mk_fft.cu), pass by pass: radix-8
-// passes, then one radix-2 or radix-4 pass when log2 nt is not a multiple of
-// 3; pass (R, Ns) stores e^{-2 pi i r k / (Ns R)} at [(r - 1) Ns + k],
-// r = 1 .. R-1, k < Ns, tables back to back (nt - 1 entries).  FP64, rounded.
-void fill_twiddles(std::vector<float2>& tw, int nt) {
-  int lg = 0;
-  while ((1 << lg) < nt) ++lg;
-  int Ns = 1, toff = 0;
-  auto pass = [&](int R) {
-    for (int r = 1; r < R; ++r)
-      for (int k = 0; k < Ns; ++k) {
-        const long long q = (long long)r * k * (nt / (Ns * R));  // exponent in units of 1/nt
-        const double a = -2.0 * M_PI * (double)q / (double)nt;
-        tw[toff + (r - 1) * Ns + k] = make_float2((float)cos(a), (float)sin(a));
-      }
-    toff += (R - 1) * Ns;
-    Ns *= R;
-  };
-  for (int p = 0; p < lg / 3; ++p) pass(8);
-  if (lg % 3 == 1) pass(2);
-  if (lg % 3 == 2) pass(4);
 }
 
 mk_status get_survey(mk_plan_t p, int32_t survey, Survey** out) {
@@ -291,12 +279,22 @@ TimedPair* next_pair(mk_plan_t p, int kind) {
 // host memory, R arrives in chunks of chunk_w frequencies on the survey's
 // copy stream, double-buffered: the copy of chunk c + 1 overlaps the
 // contraction of chunk c (each chunk is an independent set of frequencies).
-mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch) {
+// iteration: the contraction of a Neumann iteration (its output joins the pmin
+// spectrum where the survey keeps one).
+mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch, bool iteration = false) {
   if (!sv.stream_r) {
-    MK_CUDA(p, mk::launch_contract(sv.dev, sv.umma, st, p->num_sms, nlaunch));
+    mk::SurveyDev v = sv.dev;
+    // the GEMV may stream R before the preceding kernel ends only when that
+    // kernel cannot have written R
+    v.pdl = sv.r_written ? 0 : 1;
+    v.pacc = iteration ? sv.pacc : nullptr;
+    sv.r_written = false;
+    MK_CUDA(p, mk::launch_contract(v, sv.umma, st, p->num_sms, nlaunch));
     return MK_OK;
   }
   mk::SurveyDev v = sv.dev;
+  v.pdl = 0;
+  v.pacc = nullptr;
   const size_t row = (size_t)v.ns * v.r_pad;  // complex elements per frequency
   *nlaunch = 0;
   int c = 0;
@@ -495,6 +493,14 @@ mk_status materialize(mk_plan_t p, Survey& sv, uint32_t mask) {
   const size_t field = (size_t)v.F * v.ns * v.nt * sizeof(float);
   if (sv.iter == 0) {
     MK_CUDA(p, cudaMemsetAsync(v.pmin, 0, field, p->stream));
+  } else if (sv.pacc_valid) {
+    // pmin = sum of the iterations' synthesis results: one inverse transform of
+    // their summed band spectra
+    mk::SurveyDev w = v;
+    w.S = sv.pacc;
+    MK_CUDA(p, mk::launch_inverse(w, v.pmin, 1, p->stream, p->num_sms));
+    p->stats.launches++;
+    p->stats.other_launches++;
   } else {
     int nl = 0;
     MK_CUDA(p, mk::launch_spectrum(v, v.scratch, p->stream, p->num_sms));
@@ -594,11 +600,9 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
         return fail(nullptr, MK_ERR_CUDA, "tensor map encoding for the tensor-core contraction failed");
       }
     }
-    const int nt = sv.dev.nt;
-    std::vector<float2> tw(nt, make_float2(0.f, 0.f));
-    fill_twiddles(tw, nt);
-    e = cudaMemcpyAsync(const_cast<float2*>(sv.dev.tw), tw.data(), nt * sizeof(float2), cudaMemcpyHostToDevice,
-                        p->stream);
+    // the FFT twiddle table, formed on the device (the same generator serves
+    // every entry point)
+    e = mk::launch_twiddles(const_cast<float2*>(sv.dev.tw), sv.dev.nt, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
       for (auto& o : p->s) mk::umma_destroy(o.umma);
@@ -680,6 +684,9 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
       p->stats.other_launches++;
     }
   }
+  sv->r_written = true;
+  sv->pacc_valid = false;  // a series continued on new R: pmin follows from the current R
+  sv->derived_valid = sv->gm_valid = sv->gp_valid = false;
   if (src_on_device == MK_SRC_HOST) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   for (int m = w_begin; m < w_begin + w_count; ++m) {
     if (!sv->loaded[m]) {
@@ -741,6 +748,9 @@ mk_status mk_load_R_time(mk_plan_t p, int32_t survey, const float* Rt, int32_t s
     p->stats.launches++;
     p->stats.other_launches++;
   }
+  sv->r_written = true;
+  sv->pacc_valid = false;
+  sv->derived_valid = sv->gm_valid = sv->gp_valid = false;
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   for (int m = 0; m < v.nw; ++m) sv->loaded[m] = 1;
   sv->nloaded = v.nw;
@@ -824,9 +834,12 @@ mk_status mk_set_Gd_window(mk_plan_t p, int32_t survey, const float* Gd, const d
   }
   MK_CUDA(p, mk::launch_init(v, gsrc, p->stream, p->num_sms));
   MK_CUDA(p, mk::launch_set_iter(v, 0, p->stream));
+  if (sv->pacc)
+    MK_CUDA(p, cudaMemsetAsync(sv->pacc, 0, (size_t)v.nw * v.s_stride * sizeof(float2), p->stream));
   p->stats.launches += 3;
   p->stats.other_launches += 3;
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  sv->pacc_valid = sv->pacc != nullptr;
   sv->ready = true;
   sv->iter = 0;
   sv->n_in_field = true;
@@ -852,7 +865,7 @@ mk_status launch_iteration(mk_plan_t p, bool timed, cudaStream_t main, bool bran
     TimedPair* tp = timed ? next_pair(p, 0) : nullptr;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
     int nl = 0;
-    mk_status cs = contract(p, sv, st, &nl);
+    mk_status cs = contract(p, sv, st, &nl, true);
     if (cs != MK_OK) return cs;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->b, st));
     tp = timed ? next_pair(p, 1) : nullptr;
@@ -1034,6 +1047,7 @@ mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float*
   p->stats.other_launches += 2;
   if (!src_on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
   sv->iter = iteration;
+  sv->pacc_valid = false;  // pmin of resumed fields follows from the synthesis at fetch
   sv->n_in_field = true;
   sv->derived_valid = sv->gm_valid = sv->gp_valid = false;
   return MK_OK;

@@ -23,7 +23,7 @@
 // transform of X + iY with Hermitian X, Y gives x + iy; the forward transform
 // Z of a + ib gives A_m = (Z_m + conj Z_{-m})/2, B_m = (Z_m - conj Z_{-m})/(2i).
 // The complex transform is a Stockham autosort FFT in shared memory with
-// twiddles from an FP64 host table rounded to FP32 (radix-8 passes,
+// twiddles from an FP64 table rounded to FP32 (radix-8 passes,
 // contiguous per-pass twiddle tables and a padded shared-memory index keep
 // the accesses bank-conflict free).  The epilogue and the band kernel
 // (initialisation, field spectra) take blocks of up to 8 consecutive traces:
@@ -213,7 +213,7 @@ __device__ __forceinline__ float2* fft_smem_pp(float2* a, float2* b, const float
 // In-place complex DFT of x[P(0 .. NT-1)] (unnormalised; sign -1 forward,
 // +1 inverse): radix-8 passes, then one radix-2 or radix-4 pass when log2 NT
 // is not a multiple of 3.  The twiddle table holds the passes' tables back to
-// back (NT - 1 entries in all, see fill_twiddles on the host).
+// back (NT - 1 entries in all, see twiddle_kernel).
 template <int NT, int THREADS, bool INV>
 __device__ __forceinline__ void fft_smem(float2* x, const float2* tw) {
   constexpr int LOG2 = ilog2(NT);
@@ -932,6 +932,39 @@ bool epilogue_fits(int nt, int nw) {
     default: return false;
   }
   return bytes <= (size_t)kEpiSmemMax;
+}
+
+// FFT twiddles in the pass-by-pass layout the shared-memory FFT reads
+// (radix-8 passes, then one radix-2 or radix-4 pass when log2 nt is not a
+// multiple of 3): pass (R, Ns) at offset toff stores e^{-2 pi i r k / (Ns R)}
+// at toff + (r - 1) Ns + k, r = 1 .. R-1, k < Ns; nt - 1 entries, the last slot
+// zero.  Each value is formed in FP64 (sincospi of the exact rational angle)
+// and rounded to FP32.
+__global__ void twiddle_kernel(float2* tw, int nt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nt) return;
+  int lg = 0;
+  while ((1 << lg) < nt) ++lg;
+  int Ns = 1, toff = 0;
+  for (int p = 0; p < lg / 3 + (lg % 3 ? 1 : 0); ++p) {
+    const int R = p < lg / 3 ? 8 : (lg % 3 == 1 ? 2 : 4);
+    if (e < toff + (R - 1) * Ns) {
+      const int r = (e - toff) / Ns + 1, k = (e - toff) % Ns;
+      const long long q = (long long)r * k * (nt / (Ns * R));  // angle in units of 2 pi / nt
+      double sv, cv;
+      sincospi(-2.0 * (double)q / (double)nt, &sv, &cv);
+      tw[e] = make_float2((float)cv, (float)sv);
+      return;
+    }
+    toff += (R - 1) * Ns;
+    Ns *= R;
+  }
+  tw[e] = make_float2(0.f, 0.f);
+}
+
+cudaError_t launch_twiddles(float2* tw, int nt, cudaStream_t st) {
+  twiddle_kernel<<<(nt + 255) / 256, 256, 0, st>>>(tw, nt);
+  return cudaGetLastError();
 }
 
 __global__ void set_iter_kernel(int* it, int v) { *it = v; }

@@ -178,7 +178,7 @@ template <int PER>
 __global__ void __launch_bounds__(kBulkThreads, 1)
 gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S, int ns,
                  int rq, int64_t nw_stride4, int64_t s_stride, float c, int nw, int stages,
-                 unsigned* __restrict__ queue, int* __restrict__ err) {
+                 unsigned* __restrict__ queue, int* __restrict__ err, float2* __restrict__ pacc) {
   extern __shared__ __align__(128) float4 ring[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
@@ -293,7 +293,15 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
           re += __shfl_xor_sync(0xffffffffu, re, o);
           im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+        if (lane == 0) {
+          const float2 v = make_float2(c * re, c * im);
+          S[(int64_t)w * s_stride + k] = v;
+          if (pacc) {  // pmin += s_i, kept as a band spectrum (one lane owns each (m, k))
+            float2* pa = pacc + (int64_t)w * s_stride + k;
+            const float2 o = *pa;
+            *pa = make_float2(o.x + v.x, o.y + v.y);
+          }
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
@@ -322,8 +330,12 @@ cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   const size_t smem = (size_t)stages * kConsWarps * rq * 16;
   const int64_t units = (int64_t)s.nw * ((s.ns + kUnitRows - 1) / kUnitRows);
   const int64_t grid = units < num_sms ? units : num_sms;  // every CTA has a first unit
-  // programmatic dependent launch: the CTAs may start on SMs the previous
-  // kernel has left while its last CTAs finish
+  // programmatic dependent launch (when the host allows it, s.pdl): the CTAs
+  // may start on SMs the previous kernel has left while its last CTAs finish,
+  // and stream their first unit of R before that kernel ends.  The host
+  // allows it only when the preceding kernel writes no R (normally the
+  // epilogue); after an R load the launch is an ordinary stream-ordered one,
+  // for which griddepcontrol.wait returns at once.
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kBulkThreads);
@@ -333,10 +345,10 @@ cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = s.pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, gemv_bulk_kernel<PER>, reinterpret_cast<const float4*>(s.R),
                             reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq, s.nw_stride / 2, s.s_stride, s.c,
-                            s.nw, stages, s.counter + 1, s.err);
+                            s.nw, stages, s.counter + 1, s.err, s.pacc);
 }
 
 template <int PER>

@@ -53,6 +53,13 @@ struct SurveyDev {
   int* err;           // device error word (bounded waits that ran out); may be null
   int* iter;          // device iteration index (parity and energy slot; advanced by the epilogue)
   int epi_g;          // epilogue pairs per block: 0 = chosen from shared memory and grid size, else 1, 2 or 4
+  // Host-side launch choices (not read by kernels except where noted):
+  int pdl;            // 1: the F = 1 contraction may start as a programmatic dependent of the
+                      // preceding kernel, streaming R before that kernel ends; the host sets it
+                      // only when no kernel that writes R can precede it on the stream
+  float2* pacc;       // null, or [nw][s_stride] running sum of the contraction outputs S of the
+                      // Neumann iterations (the band spectrum of pmin, Algorithm 1), added to by
+                      // the F = 1 contraction
 };
 
 // Kernel launchers (return the launch status; the caller checks it).
@@ -69,6 +76,7 @@ cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t ro
 // Energies of iteration i go to ring[(i % slots) * F + f].
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
 cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);
+cudaError_t launch_twiddles(float2* tw, int nt, cudaStream_t st);  // FFT twiddle table of nt entries
 bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the per-CTA limit
 int epilogue_max_pairs(int nt, int nw);  // largest pairs-per-block the epilogue's shared memory allows
 bool umma_set_bn(UmmaMaps* mp, const SurveyDev& s, int bn);  // N tile of the tensor-core contraction

@@ -58,29 +58,17 @@ mk_status setup_device(int dev, void** out) {
   return MK_OK;
 }
 
-// FFT twiddles in the pass-by-pass layout of mk_fft.cu (radix-8 passes, then
-// radix 2 or 4): entry e of pass (R, Ns) at offset toff is
-// e^{-2 pi i r k / (Ns R)} with r = (e - toff) / Ns + 1, k = (e - toff) mod Ns.
-__global__ void twiddle_kernel(float2* tw, int nt) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= nt) return;
-  int lg = 0;
-  while ((1 << lg) < nt) ++lg;
-  int Ns = 1, toff = 0;
-  for (int p = 0; p < lg / 3 + (lg % 3 ? 1 : 0); ++p) {
-    const int R = p < lg / 3 ? 8 : (lg % 3 == 1 ? 2 : 4);
-    if (e < toff + (R - 1) * Ns) {
-      const int r = (e - toff) / Ns + 1, k = (e - toff) % Ns;
-      const long long q = (long long)r * k * (nt / (Ns * R));
-      double sv, cv;
-      sincospi(-2.0 * (double)q / (double)nt, &sv, &cv);
-      tw[e] = make_float2((float)cv, (float)sv);
-      return;
-    }
-    toff += (R - 1) * Ns;
-    Ns *= R;
-  }
-  tw[e] = make_float2(0.f, 0.f);  // the table has nt - 1 entries; the last slot is unused
+// A device time-out of the contraction (its bounded waits) sets the error
+// word; the call does not wait for the GPU, so instead of a status the
+// outputs are overwritten with NaN, which no valid result contains.
+__global__ void poison_kernel(const int* __restrict__ err, float* __restrict__ fields, size_t nf,
+                              double* __restrict__ energy, size_t ne) {
+  if (*err == 0) return;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) fields[i] = __int_as_float(0x7fc00000);
+  if (energy)
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += stride)
+      energy[i] = __longlong_as_double(0x7ff8000000000000LL);
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -129,7 +117,8 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   const size_t c_bytes = 256;
   const size_t tw_bytes = align256((size_t)v.nt * sizeof(float2));
   const size_t slot_bytes = align256((size_t)v.F * sizeof(double));
-  const size_t need = nw_bytes + s_bytes + l_bytes + e_bytes + c_bytes + tw_bytes + slot_bytes + 256;
+  const size_t err_bytes = 256;
+  const size_t need = nw_bytes + s_bytes + l_bytes + e_bytes + c_bytes + tw_bytes + slot_bytes + err_bytes + 256;
   if (need > MK_NOALLOC_SCRATCH_BYTES) {
     char buf[256];
     snprintf(buf, sizeof buf,
@@ -163,6 +152,8 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   off += c_bytes;
   v.iter = reinterpret_cast<int*>(base + off);  // starts at 0 (cleared below)
   off += 256;
+  v.err = reinterpret_cast<int*>(base + off);   // error word of the bounded waits (cleared below)
+  off += err_bytes;
   float2* tw = reinterpret_cast<float2*>(base + off);
   off += tw_bytes;
   double* slot = reinterpret_cast<double*>(base + off);
@@ -182,8 +173,8 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   // reads before writing (Nw padding, S padding, completion counter).
   if ((e = cudaMemsetAsync(base, 0, off, stream)) != cudaSuccess)
     return set_err(MK_ERR_CUDA, "cudaMemsetAsync failed", cudaGetErrorString(e));
-  twiddle_kernel<<<(v.nt + 255) / 256, 256, 0, stream>>>(tw, v.nt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return set_err(MK_ERR_CUDA, "twiddle launch", cudaGetErrorString(e));
+  if ((e = mk::launch_twiddles(tw, v.nt, stream)) != cudaSuccess)
+    return set_err(MK_ERR_CUDA, "twiddle launch", cudaGetErrorString(e));
   if ((e = mk::launch_windows(v, td, eps_s, stream)) != cudaSuccess)
     return set_err(MK_ERR_CUDA, "window launch", cudaGetErrorString(e));
   if ((e = mk::launch_init(v, Gd, stream, num_sms)) != cudaSuccess)
@@ -212,5 +203,7 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
         (e = mk::launch_inverse(v, v.pmin, 1, stream, num_sms)) != cudaSuccess)
       return set_err(MK_ERR_CUDA, "pmin synthesis launch", cudaGetErrorString(e));
   }
+  poison_kernel<<<num_sms * 4, 256, 0, stream>>>(v.err, fields, 5 * field, energy, energy ? (size_t)niter * v.F : 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return set_err(MK_ERR_CUDA, "error check launch", cudaGetErrorString(e));
   return MK_OK;
 }

@@ -316,3 +316,53 @@ def test_graph_replay_matches_stream_launches(tiny_inputs):
         p.close()
     for a, b in zip(outs[0], outs[1]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("nfocal", [1, 3])
+def test_new_R_between_iterations(nfocal):
+    # mk_load_R of a second R (from device memory, so a load kernel precedes the
+    # next contraction on the stream) between iterations, without a new
+    # mk_set_Gd_window: the series continues from its state with the new R, and
+    # the first contraction after the load must read the new R
+    import torch
+    s = small_survey(n=33, nt=128, nfocal=nfocal)
+    R1, td, Gd = survey_inputs(s)
+    s2 = small_survey(n=33, nt=128, nfocal=nfocal, seed=11, calibrate=0.6)
+    R2 = S.reflection_band(s2, dtype=np.complex64)
+    c = s.dx * s.dt
+    theta = M.theta_mask(td, s.eps, s.nt, s.dt)
+    st = M.initialise(Gd.astype(np.float64))
+    for _ in range(2):
+        st = M.iterate_once(st, R1.astype(np.complex128), theta, c)
+    for _ in range(3):
+        st = M.iterate_once(st, R2.astype(np.complex128), theta, c)
+    p = _plan(s, R1, Gd, td)
+    p.iterate(2)
+    p.load_R(0, torch.from_numpy(R2).cuda())
+    e = p.iterate(3)
+    f = p.fetch_fields(0)
+    p.close()
+    ref = [st.N, st.f1plus, st.f1min, st.f2p]
+    for j, name in enumerate(FIELD_NAMES[:4]):
+        err = rel_l2(f[j], ref[j])
+        assert err <= (TOL_N if name == "N" else TOL_ITER), f"F={nfocal} {name}: {err:.3e}"
+    # pmin after a change of R is formed with the current R: synthesis of f2p - N_last
+    pmin = M.synthesis(R2.astype(np.complex128), st.f2p - st.N, c)
+    assert rel_l2(f[4], pmin) <= TOL_ITER
+    assert rel_l2(f[5], M.total_green(st.f2p, pmin)) <= TOL_ITER
+    assert np.max(np.abs(e[-1] - st.energy[-1]) / st.energy[-1]) <= TOL_E
+
+
+@pytest.mark.parametrize("fmax", [None, 60.0])
+def test_longest_traces_nt8192(fmax):
+    # nt = 8192, the longest trace the library accepts (its own epilogue shape:
+    # 512 threads, one CTA per SM, in-place transforms), per iteration
+    s = small_survey(n=9, dx=20.0, nt=8192, dt=0.0005, nfocal=2, fmax_hz=fmax)
+    R, td, Gd = survey_inputs(s)
+    _, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 4, history=True)
+    p = _plan(s, R, Gd, td)
+    for i in range(4):
+        e = p.iterate(1)
+        _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"nt=8192 fmax={fmax} iter {i}")
+        assert np.max(np.abs(e[0] - hist[i].energy[i]) / hist[i].energy[i]) <= TOL_E
+    p.close()
