@@ -5,7 +5,9 @@ and ``bench.py`` (its ``cpu_baseline`` leg and ``--impl reference``) may import
 it.  It shares no code with the CUDA path and imports nothing from the product
 package; its inputs come from the ``synthetic`` generators.
 
-It is the paper's algorithm written out plainly in NumPy float64/complex128,
+It is the paper's algorithm written out plainly in NumPy float64/complex128
+(plus one plain-C loop, ``csynth.c``, for the contraction of surveys whose
+dense FP64 R does not fit in memory),
 step by step in the order of Algorithm 1, with the synthesis of Eq. (1) done
 in the frequency domain as the paper's Theory section states (forward DFT of
 the field, per-frequency product with R and integral over the surface
@@ -99,6 +101,21 @@ def synthesis(Rw: np.ndarray, N: np.ndarray, c: float) -> np.ndarray:
     return inverse_band(synthesis_spectrum(Rw, N, c), N.shape[-1])
 
 
+def synthesis_factored(Rf, N: np.ndarray, c: float) -> np.ndarray:
+    """``synthesis`` for a reflection response given by its two factors,
+    Rf = (T [n_w][n] complex, g [n][n] real) with R_m(k, r) = T[m][|k-r|] g[k][r]:
+    the same steps (forward DFT of N, the per-frequency sum over r of Eq. 1,
+    inverse DFT), with R rebuilt element by element inside a plain C loop
+    instead of held as a dense array (surveys whose FP64 R does not fit in
+    memory)."""
+    from . import _clib
+    T, g = Rf
+    nw = T.shape[0]
+    Nw = np.ascontiguousarray(np.transpose(forward_band(N, nw), (2, 1, 0)))  # [m][r][F]
+    S = _clib.contract_factored(T, g, Nw, c)                                  # [m][k][F]
+    return inverse_band(np.transpose(S, (2, 1, 0)), N.shape[-1])
+
+
 def synthesis_spectrum(Rw: np.ndarray, N: np.ndarray, c: float) -> np.ndarray:
     """The band spectrum S[F][k][m] of ``synthesis`` (same steps, before the
     inverse transform)."""
@@ -139,11 +156,13 @@ def initialise(Gd: np.ndarray) -> State:
     return State(N=N.copy(), f1plus=N.copy(), f1min=z.copy(), f2p=N.copy(), pmin=z.copy())
 
 
-def iterate_once(st: State, Rw: np.ndarray, theta: np.ndarray, c: float) -> State:
+def iterate_once(st: State, Rw, theta: np.ndarray, c: float, synth=None) -> State:
     """One Neumann iteration, in the order of Algorithm 1:
     iRN = synthesis(N_{i-1}); pmin += iRN; N_i = -iRN(-t); mute N_i;
-    f2p += N_i; iteration even: f1min -= N_i(-t); odd: f1plus += N_i."""
-    iRN = synthesis(Rw, st.N, c)
+    f2p += N_i; iteration even: f1min -= N_i(-t); odd: f1plus += N_i.
+    ``synth`` is the synthesis of Eq. (1) to use (default ``synthesis`` on a
+    dense Rw; ``synthesis_factored`` for R given by its factors)."""
+    iRN = (synthesis if synth is None else synth)(Rw, st.N, c)
     st.pmin = st.pmin + iRN
     Ni = -reverse_time(iRN)
     Ni = Ni * theta

@@ -22,6 +22,7 @@ from .layered import (  # noqa: F401
     jitter_matrix,
     random_model,
     reflection_band,
+    reflection_factors,
     ricker_spectrum,
     ricker_wavelet,
     signed_times,

@@ -230,20 +230,33 @@ def amplitude_scale(s: Survey) -> float:
     return s.meta["kappa"]
 
 
+def reflection_factors(s: Survey, w_begin: int = 0, w_count: int | None = None, rows=None):
+    """The two factors of R: (T [w_count][n] complex128, g [len(rows)][n] float64)
+    with R_m(k, r) = T[m][|k - r|] * g[k][r] -- the offset spectra of the
+    flat-layered primaries and the reciprocal jitter scale
+    g(k, r) = (1 + 0.01 u(k, r)) kappa / dt.  ``reflection_band`` is their
+    product; a consumer that cannot hold R whole rebuilds any element from them."""
+    if w_count is None:
+        w_count = s.nw - w_begin
+    T = _offset_spectra(s, w_begin, w_count)
+    g = (1.0 + 0.01 * jitter_matrix(s.seed, s.n, rows)) * (amplitude_scale(s) / s.dt)
+    return T, g
+
+
 def reflection_band(s: Survey, w_begin: int = 0, w_count: int | None = None,
                     dtype=np.complex128, rows=None, chunk: int = 16) -> np.ndarray:
     """Band spectra of R, shape [w_count][len(rows)][n], frequency-major.
 
     R_m(k, r) = (kappa/dt) (1 + 0.01 u(k, r)) sum_i A_i(h) W(f_m) exp(-2 pi i f_m t_i(h)),
     h = |x_k - x_r|, with u the reciprocal jitter of ``jitter_matrix`` and
-    kappa the calibration of ``amplitude_scale``.
+    kappa the calibration of ``amplitude_scale`` (the product of the factors
+    of ``reflection_factors``).
     """
     if w_count is None:
         w_count = s.nw - w_begin
     rows = np.arange(s.n) if rows is None else np.asarray(rows)
-    T = _offset_spectra(s, w_begin, w_count)
+    T, scale = reflection_factors(s, w_begin, w_count, rows)
     off = np.abs(rows[:, None] - np.arange(s.n)[None, :])
-    scale = (1.0 + 0.01 * jitter_matrix(s.seed, s.n, rows)) * (amplitude_scale(s) / s.dt)
     out = np.empty((w_count, rows.size, s.n), dtype=dtype)
     for c in range(0, w_count, chunk):
         e = min(w_count, c + chunk)

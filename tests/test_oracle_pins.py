@@ -206,6 +206,35 @@ def pin_accumulation_identities(tiny_inputs, niter):
 # tests
 # --------------------------------------------------------------------------
 
+@pytest.mark.parametrize("nt,dt,fmax,expect", [
+    (512, 0.004, None, 257),      # tiny survey: full band 0 .. nt/2
+    (2048, 0.004, 60.0, 492),     # paper-small: 60 Hz * 8.192 s = 491.52 -> bins 0 .. 491
+    (4096, 0.004, 60.0, 984),     # large survey: 60 Hz * 16.384 s = 983.04 -> bins 0 .. 983
+    (64, 0.004, 1000.0, 33),      # above Nyquist: capped at nt/2
+    (1000 // 8 * 8, 0.002, 0.0, 501),  # fmax <= 0 keeps the full band
+    (128, 0.008, 40.0, 41),       # 40 Hz * 1.024 s = 40.96 -> bins 0 .. 40
+    (128, 0.0078125, 32.0, 33),   # exactly on a bin: 32 Hz * 1 s = 32 -> bins 0 .. 32 kept
+])
+def test_band_bins_closed_forms(nt, dt, fmax, expect):
+    # the kept band ("padding" of the Implementation section): every bin m with
+    # f_m = m / (nt dt) <= fmax up to Nyquist, counted here by brute force in
+    # exact rationals
+    from fractions import Fraction
+    assert M.band_bins(nt, dt, fmax) == expect
+    if fmax:
+        T = Fraction(nt) * Fraction(dt)
+        brute = sum(1 for m in range(nt // 2 + 1) if Fraction(m) / T <= Fraction(fmax))
+        assert brute == expect
+
+
+def test_band_bins_of_every_workload():
+    # the oracle's band equals the inputs' band on every seeded workload
+    import synthetic as S
+    surveys = [S.tiny_survey(), S.paper_small_survey(1), S.large_survey(1)] + S.batching_surveys()
+    for sv in surveys:
+        assert M.band_bins(sv.nt, sv.dt, sv.fmax_hz) == S.band_count(sv.nt, sv.dt, sv.fmax_hz) == sv.nw
+
+
 def test_forward_band_matches_naive_dft():
     rng = np.random.default_rng(0)
     x = rng.standard_normal((3, 64))
@@ -438,3 +467,61 @@ def test_image_brute_force(tiny_inputs):
             acc += Gm[0, k, j] * st.f1plus[0, k, (nt - j) % nt]
     sub = Gm[:, ::25], st.f1plus[:, ::25]
     assert abs(M.image(*sub, s.dx, s.dt)[0] - s.dx * s.dt * acc) < 1e-12 * abs(acc) * s.dx * s.dt + 1e-300
+
+
+# --------------------------------------------------------------------------
+# the factored-R synthesis (plain C contraction) of the large-survey checks
+# --------------------------------------------------------------------------
+
+def _factored_case(n=7, nt=32, nw=13, F=3, seed=5):
+    rng = np.random.default_rng(seed)
+    T = rng.standard_normal((nw, n)) + 1j * rng.standard_normal((nw, n))
+    g = 1.0 + 0.3 * rng.standard_normal((n, n))          # not symmetric: pins which index is which
+    N = rng.standard_normal((F, n, nt))
+    off = np.abs(np.arange(n)[:, None] - np.arange(n)[None, :])
+    R = T[:, off] * g[None]                               # R_m(k, r) = T[m][|k - r|] g[k][r]
+    return T, g, N, R
+
+
+def test_factored_synthesis_matches_brute_force():
+    # Eq. (1) as a time-domain circular convolution with the band-limited R
+    T, g, N, R = _factored_case()
+    nt = N.shape[-1]
+    Rbl = naive_real_idft(R.transpose(1, 2, 0), nt)
+    got = M.synthesis_factored((T, g), N, 0.37)
+    assert rel_l2(got, brute_synthesis(Rbl, N, 0.37)) < 1e-12
+
+
+def test_factored_synthesis_matches_dense_on_a_survey():
+    # the generator's dense R (the product of its factors) through the NumPy
+    # oracle vs the factors through the C contraction
+    s = small_survey(n=25, nt=128, nfocal=3, fmax_hz=40.0)
+    T, g = S.reflection_factors(s)
+    R = S.reflection_band(s)
+    td = S.survey_td(s)
+    N = M.reverse_time(S.gd_traces(s, td, np.float64))
+    c = s.dx * s.dt
+    assert rel_l2(M.synthesis_factored((T, g), N, c), M.synthesis(R, N, c)) < 1e-13
+
+
+def test_factored_synthesis_catches_transposed_scale():
+    # a transposed jitter scale (g[r][k] for g[k][r]) must change the result
+    T, g, N, R = _factored_case()
+    ref = M.synthesis(R, N, 1.0)
+    assert rel_l2(M.synthesis_factored((T, g.T.copy()), N, 1.0), ref) > 1e-3
+    assert rel_l2(M.synthesis_factored((T, g), N, 1.0), ref) < 1e-13
+
+
+def test_factored_iteration_follows_algorithm_1(tiny_inputs):
+    # the iteration with the factored synthesis equals the dense one
+    s, R, td, Gd = tiny_inputs
+    T, g = S.reflection_factors(s)
+    theta = M.theta_mask(td, s.eps, s.nt, s.dt)
+    c = s.dx * s.dt
+    a = M.initialise(Gd)
+    b = M.initialise(Gd)
+    for _ in range(3):
+        a = M.iterate_once(a, R, theta, c)
+        b = M.iterate_once(b, (T, g), theta, c, synth=M.synthesis_factored)
+    for x, y in ((a.N, b.N), (a.f1plus, b.f1plus), (a.f1min, b.f1min), (a.pmin, b.pmin)):
+        assert rel_l2(y, x) < 1e-12
