@@ -31,11 +31,22 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
   return v;
 }
 
+// S at index i; with pacc also pmin += s_i, kept as a band spectrum (one lane
+// owns each (m, k), so the update is race-free).
+__device__ __forceinline__ void store_s(float2* S, float2* pacc, int64_t i, float2 v) {
+  S[i] = v;
+  if (pacc) {
+    const float2 o = pacc[i];
+    pacc[i] = make_float2(o.x + v.x, o.y + v.y);
+  }
+}
+
 // Rows of RQ float4 (two complex each); lane l owns float4 l, l + 32, ...
 template <int PER>
 __global__ void __launch_bounds__(256)
 gemv_c64_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S,
-                int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows) {
+                int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows,
+                float2* __restrict__ pacc) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -79,14 +90,15 @@ gemv_c64_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, flo
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+    if (lane == 0) store_s(S, pacc, (int64_t)w * s_stride + k, make_float2(c * re, c * im));
   }
 }
 
 // Rows longer than the register-resident form: Nw is re-read through L1.
 __global__ void __launch_bounds__(256)
 gemv_c64_long_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S,
-                     int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows) {
+                     int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows,
+                     float2* __restrict__ pacc) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -123,7 +135,7 @@ gemv_c64_long_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+    if (lane == 0) store_s(S, pacc, (int64_t)w * s_stride + k, make_float2(c * re, c * im));
   }
 }
 
@@ -293,15 +305,7 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
           re += __shfl_xor_sync(0xffffffffu, re, o);
           im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) {
-          const float2 v = make_float2(c * re, c * im);
-          S[(int64_t)w * s_stride + k] = v;
-          if (pacc) {  // pmin += s_i, kept as a band spectrum (one lane owns each (m, k))
-            float2* pa = pacc + (int64_t)w * s_stride + k;
-            const float2 o = *pa;
-            *pa = make_float2(o.x + v.x, o.y + v.y);
-          }
-        }
+        if (lane == 0) store_s(S, pacc, (int64_t)w * s_stride + k, make_float2(c * re, c * im));
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
@@ -367,7 +371,7 @@ cudaError_t launch_gemv_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   if (grid * 8 > total) grid = (total + 7) / 8;
   gemv_c64_kernel<PER><<<(unsigned)grid, 256, 0, st>>>(
       reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns,
-      s.r_pad / 2, s.nw_stride / 2, s.s_stride, s.c, total);
+      s.r_pad / 2, s.nw_stride / 2, s.s_stride, s.c, total, s.pacc);
   return cudaGetLastError();
 }
 
@@ -413,7 +417,7 @@ cudaError_t launch_gemv(const SurveyDev& s, cudaStream_t st, int num_sms) {
       if (grid * 8 > total) grid = (total + 7) / 8;
       gemv_c64_long_kernel<<<(unsigned)grid, 256, 0, st>>>(
           reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq,
-          s.nw_stride / 2, s.s_stride, s.c, total);
+          s.nw_stride / 2, s.s_stride, s.c, total, s.pacc);
       return cudaGetLastError();
     }
   }
