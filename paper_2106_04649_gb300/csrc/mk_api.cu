@@ -194,10 +194,12 @@ size_t layout(Survey& sv, char* base) {
     v.Bq2 = d.rprec == MK_R_SPLIT3_BF16 ? take(bq) : nullptr;
   }
   v.S = reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)));
-  // a survey contracted by the GEMV accumulates pmin as a band spectrum during the
-  // iterations (Algorithm 1 adds every synthesis result to pmin): n_w * ns complex
-  // values, far less than R, and no extra contraction when pmin or G is fetched
-  sv.pacc = gemv_only ? reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2))) : nullptr;
+  // a survey contracted by the GEMV (complex FP32, one focal point, resident or
+  // streamed R) accumulates pmin as a band spectrum during the iterations
+  // (Algorithm 1 adds every synthesis result to pmin): n_w * ns complex values,
+  // far less than R, and no extra contraction when pmin or G is fetched
+  const bool gemv = d.rprec == MK_R_C64 && d.nfocal == 1;
+  sv.pacc = gemv ? reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2))) : nullptr;
   v.fN = reinterpret_cast<float*>(take(field));
   v.f1p = reinterpret_cast<float*>(take(field));
   v.f1m = reinterpret_cast<float*>(take(field));
@@ -294,7 +296,6 @@ mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch, bool 
   }
   mk::SurveyDev v = sv.dev;
   v.pdl = 0;
-  v.pacc = nullptr;
   const size_t row = (size_t)v.ns * v.r_pad;  // complex elements per frequency
   *nlaunch = 0;
   int c = 0;
@@ -311,6 +312,7 @@ mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch, bool 
     v.nw = cw;
     v.Nw = sv.dev.Nw + (size_t)w0 * v.nw_stride;
     v.S = sv.dev.S + (size_t)w0 * v.s_stride;
+    v.pacc = iteration && sv.pacc ? sv.pacc + (size_t)w0 * v.s_stride : nullptr;
     int nl = 0;
     MK_CUDA(p, mk::launch_contract(v, nullptr, st, p->num_sms, &nl));
     MK_CUDA(p, cudaEventRecord(sv.free_ev[b], st));
@@ -782,6 +784,8 @@ mk_status mk_attach_R_host(mk_plan_t p, int32_t survey, const void* Rpad, size_t
     }
   }
   sv->host_r = static_cast<const float2*>(Rpad);
+  sv->pacc_valid = false;  // a series continued on new R: pmin follows from the current R
+  sv->derived_valid = sv->gm_valid = sv->gp_valid = false;
   for (int m = 0; m < v.nw; ++m) sv->loaded[m] = 1;
   sv->nloaded = v.nw;
   return MK_OK;

@@ -847,6 +847,7 @@ cudaError_t prepare_kernels() {
   cudaError_t e = prepare_contract();
   if (e != cudaSuccess) return e;
   if ((e = prepare_load()) != cudaSuccess) return e;
+  if ((e = prepare_epilogue_warp()) != cudaSuccess) return e;
 #define MK_ATTR(N) \
   if ((e = set_attrs<N>()) != cudaSuccess) return e;
   MK_ATTR(32) MK_ATTR(64) MK_ATTR(128) MK_ATTR(256) MK_ATTR(512) MK_ATTR(1024) MK_ATTR(2048)
@@ -856,6 +857,7 @@ cudaError_t prepare_kernels() {
 }
 
 int epilogue_max_pairs(int nt, int nw) {
+  if (epilogue_warp_supports(nt, nw)) return 2;  // one or two rounds of traces per block
   size_t bytes = 0;
   switch (nt) {
 #define MK_FIT(N) \
@@ -919,6 +921,7 @@ cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st) {
 }
 
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
+  if (epilogue_warp_supports(s.nt, s.nw)) return launch_epilogue_warp(s, ring, slots, st, num_sms);
 #define MK_CALL(N) launch_epi_nt<N>(s, ring, slots, st, num_sms)
   MK_NT_SWITCH(s.nt, MK_CALL)
 #undef MK_CALL

@@ -78,6 +78,12 @@ cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStr
 cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);
 cudaError_t launch_twiddles(float2* tw, int nt, cudaStream_t st);  // FFT twiddle table of nt entries
 bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the per-CTA limit
+// The epilogue with the transforms in registers, one lane group per trace (mk_epi.cu):
+// nt = 64 .. 2048 with a band whose shared stage fits; launch_epilogue uses it
+// whenever it supports the shape and falls back to the shared-memory kernel otherwise.
+bool epilogue_warp_supports(int nt, int nw);
+cudaError_t prepare_epilogue_warp();
+cudaError_t launch_epilogue_warp(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
 int epilogue_max_pairs(int nt, int nw);  // largest pairs-per-block the epilogue's shared memory allows
 bool umma_set_bn(UmmaMaps* mp, const SurveyDev& s, int bn);  // N tile of the tensor-core contraction
 int umma_get_bn(const UmmaMaps* mp);
