@@ -215,6 +215,7 @@ size_t layout(Survey& sv, char* base) {
   v.err = reinterpret_cast<int*>(take(sizeof(int)));
   v.iter = reinterpret_cast<int*>(take(sizeof(int)));
   v.tw = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));
+  v.twl = reinterpret_cast<const float2*>(take((size_t)v.nt * sizeof(float2)));
   sv.energy = reinterpret_cast<double*>(take((size_t)kMaxIterSlots * v.F * sizeof(double)));
   return off;
 }
@@ -281,15 +282,12 @@ TimedPair* next_pair(mk_plan_t p, int kind) {
 // host memory, R arrives in chunks of chunk_w frequencies on the survey's
 // copy stream, double-buffered: the copy of chunk c + 1 overlaps the
 // contraction of chunk c (each chunk is an independent set of frequencies).
-// iteration: the contraction of a Neumann iteration (its output joins the pmin
-// spectrum where the survey keeps one).
-mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch, bool iteration = false) {
+mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch) {
   if (!sv.stream_r) {
     mk::SurveyDev v = sv.dev;
     // the GEMV may stream R before the preceding kernel ends only when that
     // kernel cannot have written R
     v.pdl = sv.r_written ? 0 : 1;
-    v.pacc = iteration ? sv.pacc : nullptr;
     sv.r_written = false;
     MK_CUDA(p, mk::launch_contract(v, sv.umma, st, p->num_sms, nlaunch));
     return MK_OK;
@@ -312,7 +310,6 @@ mk_status contract(mk_plan_t p, Survey& sv, cudaStream_t st, int* nlaunch, bool 
     v.nw = cw;
     v.Nw = sv.dev.Nw + (size_t)w0 * v.nw_stride;
     v.S = sv.dev.S + (size_t)w0 * v.s_stride;
-    v.pacc = iteration && sv.pacc ? sv.pacc + (size_t)w0 * v.s_stride : nullptr;
     int nl = 0;
     MK_CUDA(p, mk::launch_contract(v, nullptr, st, p->num_sms, &nl));
     MK_CUDA(p, cudaEventRecord(sv.free_ev[b], st));
@@ -399,7 +396,7 @@ mk_status tune_survey(mk_plan_t p, Survey& sv) {
     }
     // the epilogue advances the device iteration index: start it from 0
     MK_CUDA(p, mk::launch_set_iter(v, 0, p->stream));
-    const int gmax = mk::epilogue_max_pairs(v.nt, v.nw);
+    const int gmax = mk::epilogue_max_pairs(v, p->num_sms);
     float best_ms = 1e30f;
     for (int g = 1; g <= gmax; g *= 2) {
       v.epi_g = g;
@@ -605,6 +602,7 @@ mk_status mk_plan(const mk_desc* d, int32_t ndesc, void* cuda_stream, void* work
     // the FFT twiddle table, formed on the device (the same generator serves
     // every entry point)
     e = mk::launch_twiddles(const_cast<float2*>(sv.dev.tw), sv.dev.nt, p->stream);
+    if (e == cudaSuccess) e = mk::launch_twiddles_linear(const_cast<float2*>(sv.dev.twl), sv.dev.nt, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
       for (auto& o : p->s) mk::umma_destroy(o.umma);
@@ -869,12 +867,17 @@ mk_status launch_iteration(mk_plan_t p, bool timed, cudaStream_t main, bool bran
     TimedPair* tp = timed ? next_pair(p, 0) : nullptr;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
     int nl = 0;
-    mk_status cs = contract(p, sv, st, &nl, true);
+    mk_status cs = contract(p, sv, st, &nl);
     if (cs != MK_OK) return cs;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->b, st));
     tp = timed ? next_pair(p, 1) : nullptr;
     if (tp) MK_CUDA(p, cudaEventRecord(tp->a, st));
-    MK_CUDA(p, mk::launch_epilogue(sv.dev, sv.energy, kMaxIterSlots, st, p->num_sms));
+    {
+      // the iteration's epilogue adds S to the pmin spectrum where the survey keeps one
+      mk::SurveyDev v = sv.dev;
+      v.pacc = sv.pacc;
+      MK_CUDA(p, mk::launch_epilogue(v, sv.energy, kMaxIterSlots, st, p->num_sms));
+    }
     if (tp) MK_CUDA(p, cudaEventRecord(tp->b, st));
     if (branches) {
       MK_CUDA(p, cudaEventRecord(p->join_ev[i], st));

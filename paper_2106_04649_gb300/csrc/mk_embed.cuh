@@ -40,9 +40,18 @@ __device__ __forceinline__ uint32_t pair_swap(uint32_t w) { return __byte_perm(w
 // embedding of the tensor-core contraction, split into hi + lo 16-bit parts:
 // rows 2f: (Nr, -Ni), 2f+1: (Ni, Nr) at columns 2k, 2k+1.
 template <bool BF16>
+__device__ __forceinline__ void store_embedding_at(const SurveyDev& s, int64_t e0, float nr, float ni);
+
+template <bool BF16>
 __device__ __forceinline__ void store_embedding(const SurveyDev& s, int m, int f, int k, float nr, float ni) {
   const int64_t kp = 2 * (int64_t)s.r_pad;
-  const int64_t e0 = ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k;
+  store_embedding_at<BF16>(s, ((int64_t)m * 2 * s.F + 2 * f) * kp + 2 * k, nr, ni);
+}
+
+// The same, at element offset e0 = ((m 2F + 2f) 2 r_pad + 2k) of the embedding.
+template <bool BF16>
+__device__ __forceinline__ void store_embedding_at(const SurveyDev& s, int64_t e0, float nr, float ni) {
+  const int64_t kp = 2 * (int64_t)s.r_pad;
   uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
   uint32_t* b1 = reinterpret_cast<uint32_t*>(s.Bq1);
   float hr, hi;

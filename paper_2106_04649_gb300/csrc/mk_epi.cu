@@ -22,8 +22,8 @@
 // P points in registers.  The result comes back in the same index layout
 // (k = q + P e'), so the inverse transform's output feeds the forward
 // transform directly.  Constant twiddles are compile-time 64th roots of
-// unity; per-lane twiddles are products of two values formed once per lane
-// in FP64 and rounded to FP32.
+// unity; per-lane twiddles are products of two entries of a table of
+// e^{-2 pi i j / nt} (FP64 values rounded to FP32), loaded once per lane.
 //
 // A CTA of 8 warps takes blocks of consecutive traces (focal-major order, so
 // neighbouring traces are neighbouring addresses in S and Nw): the block's
@@ -185,47 +185,52 @@ __host__ __device__ constexpr int out_e(int a) { return a / P + (32 / P) * (a % 
 template <int P>
 __host__ __device__ constexpr int out_slot(int e) { return (e % (32 / P)) * P + e / (32 / P); }
 
-// Shared buffer of one trace group (float2 elements): 32 rows of P + 1; for
-// P < 16 the groups sharing a half-warp are staggered by P elements so that
-// their transposes hit disjoint banks.
+// Shared buffer of one trace group (float2 elements): the 32 x P transpose,
+// rows of P + 1; for P < 16 the groups sharing a half-warp are staggered by
+// P elements so that their accesses hit disjoint banks.  One lane per trace
+// (P = 1) needs no transpose.
 template <int P>
-__host__ __device__ constexpr int group_buf(int /*unused*/ = 0) { return 32 * (P + 1) + (P < 16 ? P : 0); }
+__host__ __device__ constexpr int group_buf() { return P == 1 ? 0 : 32 * (P + 1) + (P < 16 ? P : 0); }
 
-// Per-lane twiddles of the M-point transform: W_M^{p k2} for k2 = 8a + b is
-// wa[a] * wb[b] (wa[a] = W_M^{8 p a}, wb[b] = W_M^{p b}, W_M = e^{-2 pi i / M}).
-struct LaneTw {
-  float2 wa[4], wb[8];
-  float2 up;  // e^{+2 pi i p / nt} (pre- and post-processing of the real transform)
-};
-
-__device__ __forceinline__ float2 tw_rounded(long long num, long long den) {  // e^{-2 pi i num / den}
-  double sv, cv;
-  sincospi(-2.0 * (double)(num % den) / (double)den, &sv, &cv);
-  return make_float2((float)cv, (float)sv);
+// Per-lane twiddle W_M^{p k2} (W_M = e^{-2 pi i / M}, M = nt/2) as the product
+// of two entries of the table e^{-2 pi i j / nt}: k2 = 8a + b,
+// W_M^{p k2} = W_M^{8 p a} W_M^{p b} (W_M^x = entry 2x mod nt).
+template <int NT>
+__device__ __forceinline__ void lane_twiddles(const float2* __restrict__ twl, int p, float2 (&wa)[4],
+                                              float2 (&wb)[8]) {
+#pragma unroll
+  for (int b = 1; b < 8; ++b) wb[b] = __ldg(twl + ((2 * p * b) & (NT - 1)));
+#pragma unroll
+  for (int a = 1; a < 4; ++a) wa[a] = __ldg(twl + ((16 * p * a) & (NT - 1)));
 }
 
 // Complex DFT of M = 32 P points over the P lanes of a group (lane p holds
 // n = p + P e at v[e]); afterwards lane q holds index k = q + P out_e(a) at
-// v[a].  gbuf is the group's shared buffer.
-template <int P, bool INV>
-__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, const LaneTw& tw) {
-  dft<32, INV>(v);  // over e: v[k2]
-  static_for<32>([&](auto K) {
-    constexpr int k2 = decltype(K)::value;
-    constexpr int a = k2 >> 3, b = k2 & 7;
-    if constexpr (k2 > 0 && P > 1) {
-      float2 w;
-      if constexpr (a == 0) {
-        w = tw.wb[b];
-      } else if constexpr (b == 0) {
-        w = tw.wa[a];
-      } else {
-        w = cmul(tw.wa[a], tw.wb[b]);
+// v[a].  gbuf is the group's shared buffer (half the transpose per pass).
+template <int NT, bool INV>
+__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, const float2* __restrict__ twl) {
+  constexpr int P = NT / 64;
+  if constexpr (P > 1) {
+    float2 wa[4], wb[8];
+    lane_twiddles<NT>(twl, p, wa, wb);
+    dft<32, INV>(v);  // over e: v[k2]
+    static_for<32>([&](auto K) {
+      constexpr int k2 = decltype(K)::value;
+      constexpr int a = k2 >> 3, b = k2 & 7;
+      if constexpr (k2 > 0) {
+        float2 w;
+        if constexpr (a == 0) {
+          w = wb[b];
+        } else if constexpr (b == 0) {
+          w = wa[a];
+        } else {
+          w = cmul(wa[a], wb[b]);
+        }
+        v[k2] = INV ? cmulc(v[k2], w) : cmul(v[k2], w);
       }
-      v[k2] = INV ? cmulc(v[k2], w) : cmul(v[k2], w);
-    }
-  });
-  if constexpr (P > 1) {  // (P = 1: 32 points, the register DFT is the whole transform)
+    });
+    // transpose: row k2 of lane n1 to column k2, which lane q = k2 mod P
+    // takes (columns k2 = q + P c)
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) gbuf[k2 * (P + 1) + p] = v[k2];
     __syncwarp();
@@ -239,6 +244,8 @@ __device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, 
       for (int k1 = 0; k1 < P; ++k1) v[c * P + k1] = t[k1];
     }
     __syncwarp();
+  } else {
+    dft<32, INV>(v);  // 32 points: the register DFT is the whole transform
   }
 }
 
@@ -257,12 +264,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// floor(x / d) and ceil(x / d) for d > 0 and any x
+__device__ __forceinline__ int floor_div(int x, int d) { return x >= 0 ? x / d : -((d - 1 - x) / d); }
+__device__ __forceinline__ int ceil_div(int x, int d) { return -floor_div(-x, d); }
+__device__ __forceinline__ int clamp32(int x) { return x < 0 ? 0 : (x > 32 ? 32 : x); }
+
 struct EpiShape {
   int rounds;  // traces per group per block (1 or 2)
   int nbuf;    // stage buffers (2: the next block loads while this one is transformed)
   int bt;      // traces per block
   size_t smem;
 };
+
+constexpr int kCtasPerSm = 2;
+constexpr size_t kSmemPerCta = 110 * 1024;  // two CTAs per SM
 
 template <int NT>
 __host__ __device__ constexpr int traces_per_warp() { return 32 / (NT / 64); }
@@ -275,8 +290,61 @@ size_t epi_smem(int nw, int rounds, int nbuf) {
          (size_t)kWarps * traces_per_warp<NT>() * group_buf<P>() * sizeof(float2) + (size_t)nbuf * bt * sizeof(int);
 }
 
+// A full block's band spectra to Nw[m][f][k0 .. k0 + bt): 16-byte stores of
+// two complex values, consecutive threads on consecutive pairs.
+__device__ __forceinline__ void store_block_nw(const SurveyDev& s, const float2* st, int ldm, int f, int k0, int bt,
+                                               int lbt) {
+  const int lq = lbt - 1;  // bt / 2 pairs per frequency
+  const int total = s.nw << lq;
+  float2* base = s.Nw + (int64_t)f * s.r_pad + k0;
+  for (int i = threadIdx.x; i < total; i += kThreads) {
+    const int m = i >> lq, q = i & ((bt >> 1) - 1);
+    const float2 a = st[m * ldm + 2 * q], b = st[m * ldm + 2 * q + 1];
+    *reinterpret_cast<float4*>(base + (int64_t)m * s.nw_stride + 2 * q) = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// A full block's band spectra into the 16-bit embedding of the tensor-core
+// contraction: NP parts (hi + lo, or hi + mid + lo), rows 2f (Nr, -Ni) and
+// 2f+1 (Ni, Nr).  A task is four consecutive positions of one frequency;
+// consecutive lanes take consecutive tasks, so each row segment of a part
+// (bt 32-bit pairs) is written by neighbouring lanes as whole 32-byte
+// sectors.  Same roundings as store_embedding.
+template <bool BF16, int NP>
+__device__ __forceinline__ void store_block_embedding(const SurveyDev& s, const float2* st, int ldm, int f, int k0,
+                                                      int bt, int lbt) {
+  const int64_t rp = s.r_pad;
+  const int lq = lbt - 2;  // bt / 4 tasks per frequency
+  const int total = s.nw << lq;
+  uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
+  uint32_t* b1 = reinterpret_cast<uint32_t*>(s.Bq1);
+  uint32_t* b2 = reinterpret_cast<uint32_t*>(s.Bq2);
+  for (int i = threadIdx.x; i < total; i += kThreads) {
+    const int m = i >> lq, q = 4 * (i & ((1 << lq) - 1));
+    const int64_t w0 = ((int64_t)m * 2 * s.F + 2 * f) * rp + k0 + q;  // 32-bit word of row 2f
+    uint32_t wd[NP][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float2 v = st[m * ldm + q + u];
+      float hr, hi, mr, mi;
+      wd[0][u] = round_pair<BF16>(v.x, v.y, hr, hi);
+      const float lr = v.x - hr, li = v.y - hi;  // exact in FP32
+      wd[1][u] = round_pair<BF16>(lr, li, mr, mi);
+      if constexpr (NP == 3) wd[2][u] = round_pair<BF16>(lr - mr, li - mi, mr, mi);
+    }
+#pragma unroll
+    for (int pp = 0; pp < NP; ++pp) {
+      uint32_t* b = pp == 0 ? b0 : (pp == 1 ? b1 : b2);
+      *reinterpret_cast<uint4*>(b + w0) =
+          make_uint4(pair_neg_hi(wd[pp][0]), pair_neg_hi(wd[pp][1]), pair_neg_hi(wd[pp][2]), pair_neg_hi(wd[pp][3]));
+      *reinterpret_cast<uint4*>(b + w0 + rp) =
+          make_uint4(pair_swap(wd[pp][0]), pair_swap(wd[pp][1]), pair_swap(wd[pp][2]), pair_swap(wd[pp][3]));
+    }
+  }
+}
+
 template <int NT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
 epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, int nbuf) {
   constexpr int M = NT / 2;
   constexpr int P = NT / 64;
@@ -300,15 +368,10 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / P, p = lane % P;
   float2* gbuf = gbufs + (warp * TPW + grp) * GB;
-
-  LaneTw tw;
-#pragma unroll
-  for (int b = 0; b < 8; ++b) tw.wb[b] = tw_rounded((long long)p * b, M);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) tw.wa[a] = tw_rounded((long long)8 * p * a, M);
+  float2 up;  // e^{+2 pi i p / nt}
   {
-    const float2 w = tw_rounded(p, NT);  // e^{-2 pi i p / nt}
-    tw.up = make_float2(w.x, -w.y);
+    const float2 w = __ldg(s.twl + p);
+    up = make_float2(w.x, -w.y);
   }
 
   const int iter = *s.iter;
@@ -316,19 +379,39 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
   double* energy_slot = ring + (int64_t)(iter % slots) * s.F;
   float* __restrict__ f1 = odd ? s.f1p : s.f1m;
   const float inv = s.inv_nt;
-  const int nblocks = (s.ncols + bt - 1) / bt;
+  // blocks never straddle focal points: block (f, kb) holds positions
+  // k0 = kb bt .. k0 + ntr - 1 of focal point f (traces t = f ns + k)
+  const int nkb = (s.ns + bt - 1) / bt;
+  const int nblocks = s.F * nkb;
   int lbt = 0;
-  while ((1 << lbt) < bt) ++lbt;  // bt is a power of two
+  while ((1 << lbt) < bt) ++lbt;  // bt is a power of two dividing kThreads
+
+  // each thread of the block passes keeps one trace column: c = tid mod bt,
+  // frequencies m = tid / bt, tid / bt + 256 / bt, ...
+  const int pc = threadIdx.x & (bt - 1);
+  const int pm0 = threadIdx.x >> lbt, pms = kThreads >> lbt;
 
   // the band spectra of block blk into stage buffer buf, asynchronously
   auto issue_load = [&](int blk, int buf) {
-    const int tb = blk * bt;
-    const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
+    const int bf = blk / nkb;
+    const int k0 = (blk - bf * nkb) * bt;
+    const int tb = bf * s.ns + k0;
+    const int ntr = s.ns - k0 < bt ? s.ns - k0 : bt;
     float2* st = stage_base + buf * stage_elems;
-    const int total = nw << lbt;
-    for (int i = threadIdx.x; i < total; i += kThreads) {
-      const int m = i >> lbt, c = i & (bt - 1);
-      if (c < ntr) cp_async8(st + (size_t)m * ldm + c, s.S + (int64_t)m * s.s_stride + tb + c);
+    if (pc < ntr && !s.pacc) {
+      const float2* src = s.S + (int64_t)pm0 * s.s_stride + tb + pc;
+      const int64_t sstep = (int64_t)pms * s.s_stride;
+      for (int m = pm0; m < nw; m += pms, src += sstep) cp_async8(st + m * ldm + pc, src);
+    } else if (pc < ntr) {
+      // the same through registers, and pmin's band spectrum += S (one thread
+      // owns each (m, t))
+      for (int m = pm0; m < nw; m += pms) {
+        const int64_t i = (int64_t)m * s.s_stride + tb + pc;
+        const float2 v = __ldg(s.S + i);
+        const float2 a = s.pacc[i];
+        st[m * ldm + pc] = v;
+        s.pacc[i] = make_float2(a.x + v.x, a.y + v.y);
+      }
     }
     int* sL = sL_base + buf * bt;
     for (int c = threadIdx.x; c < bt; c += kThreads) sL[c] = c < ntr ? s.L[tb + c] : 0;
@@ -353,117 +436,149 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
     __syncthreads();
     float2* st = stage_base + buf * stage_elems;
     const int* sL = sL_base + buf * bt;
-    const int tb = blk * bt;
-    const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
+    const int bf = blk / nkb;
+    const int k0 = (blk - bf * nkb) * bt;
+    const int tb = bf * s.ns + k0;
+    const int ntr = s.ns - k0 < bt ? s.ns - k0 : bt;
 
     for (int r = 0; r < rounds; ++r) {
       const int c = r * (kWarps * TPW) + warp * TPW + grp;  // stage column of this group's trace
       const bool active = c < ntr;
       const int L = active ? sL[c] : 0;
-      const int64_t base = (int64_t)(tb + (active ? c : 0)) * NT;
+      float* __restrict__ ft = f1 + (int64_t)(tb + (active ? c : 0)) * NT;  // this trace of f1
+      float2* col = st + c;
+      // Bounds in register index e, once per trace (inactive groups: none):
+      //  band bins k = p + P e < nw  <=>  e < ek;  M - k < nw  <=>  e >= em;
+      //  window samples j0 = 2(p + P e): j0 < L <=> e < a0, j0 > nt - L <=> e >= b0;
+      //  j1 = j0 + 1 likewise with a1, b1 (theta(j) = j < L or j > nt - L).
+      const int ek = active ? clamp32(ceil_div(nw - p, P)) : 0;
+      const int em = active ? clamp32(floor_div(M - p - nw, P) + 1) : 32;
+      const int a0 = clamp32(ceil_div(L - 2 * p, 2 * P));
+      const int b0 = active ? clamp32(floor_div(NT - L - 2 * p, 2 * P) + 1) : 32;
+      const int a1 = clamp32(ceil_div(L - 2 * p - 1, 2 * P));
+      const int b1 = active ? clamp32(floor_div(NT - L - 2 * p - 1, 2 * P) + 1) : 32;
+      const float2* colp = col + p * ldm;         // bin k = p + P e at colp[e P ldm]
+      const float2* colm = col + (M - p) * ldm;   // bin M - k at colm[-e P ldm]
+      const int pst = P * ldm;
 
-      // 1. f1 samples of this lane's outputs (window only), loaded early:
-      //    lane p ends the inverse transform with z_n at n = p + P out_e(a)
-      float fa[32], fb[32];
-#pragma unroll
-      for (int a = 0; a < 32; ++a) {
-        const int n = p + P * out_e<P>(a);
-        const int j0 = 2 * n, j1 = 2 * n + 1;
-        const bool in0 = active && (j0 < NT - j0 ? j0 : NT - j0) < L;
-        const bool in1 = active && (j1 < NT - j1 ? j1 : NT - j1) < L;
-        fa[a] = 0.f;
-        fb[a] = 0.f;
-        if (odd) {
-          if (in0) fa[a] = f1[base + ((NT - j0) & (NT - 1))];
-          if (in1) fb[a] = f1[base + (NT - j1)];
-        } else if (in0 || in1) {
-          const float2 w = reinterpret_cast<const float2*>(f1 + base)[n];
-          fa[a] = w.x;
-          fb[a] = w.y;
-        }
-      }
-
-      // 2. the half-length complex spectrum Z_k = (X_k + conj X_{M-k}) +
+      // 1. the half-length complex spectrum Z_k = (X_k + conj X_{M-k}) +
       //    i (X_k - conj X_{M-k}) e^{2 pi i k / nt}, k = p + P e, from the
       //    band spectrum X of the synthesis result (bins outside the band
       //    zero; the imaginary parts of DC and Nyquist dropped)
       float2 v[32];
       static_for<32>([&](auto E) {
         constexpr int e = decltype(E)::value;
-        const int k = p + P * e;
-        const int km = M - k;
         float2 X = make_float2(0.f, 0.f), Xm = make_float2(0.f, 0.f);
-        if (active && k < nw) X = st[(size_t)k * ldm + c];
-        if (active && km < nw) Xm = st[(size_t)km * ldm + c];
-        if (k == 0) X.y = 0.f;
-        if (km == M) Xm.y = 0.f;
+        if (e < ek) X = colp[e * pst];
+        if (e >= em) Xm = colm[-e * pst];
+        if (e == 0 && p == 0) {
+          X.y = 0.f;
+          Xm.y = 0.f;  // M - k == M: the Nyquist bin
+        }
         const float2 A = make_float2(X.x + Xm.x, X.y - Xm.y);
         const float2 B = make_float2(X.x - Xm.x, X.y + Xm.y);
-        const float2 Bt = rot64<e, true>(cmul(B, tw.up));
+        const float2 Bt = rot64<e, true>(cmul(B, up));
         v[e] = make_float2(A.x - Bt.y, A.y + Bt.x);
       });
 
-      // 3. inverse transform: z_n = x(2n) + i x(2n+1) up to the factor 1/nt
-      group_fft<P, true>(v, gbuf, p, tw);
+      // 2. inverse transform: z_n = x(2n) + i x(2n+1) up to the factor 1/nt
+      group_fft<NT, true>(v, gbuf, p, s.twl);
 
-      // 4. y = theta s; f1 update; energy; y feeds the forward transform
-      float esum = 0.f;
+      // 3. y = theta s on the window samples of this lane (the rest is zero),
+      //    its energy, and f1 on the window: even iterations
+      //    f1min(j) -= N_i(-j) = y(j), odd iterations f1plus(-j) += N_i(-j) = -y(j).
+      //    Register e of the forward input holds n = p + P e (samples 2n and
+      //    2n + 1), taken from register out_slot(e) of the inverse output.
+      //    Chunks of four registers that no lane of the warp needs in f1 skip
+      //    the f1 traffic; a chunk's loads are issued together.
       float2 w[32];
+      static_for<8>([&](auto Ch) {
+        constexpr int e0 = 4 * decltype(Ch)::value;
+        bool need[4];
+        bool any = false;
+        static_for<4>([&](auto U) {
+          constexpr int u = decltype(U)::value;
+          constexpr int e = e0 + u;
+          const bool in0 = e < a0 || e >= b0;
+          const bool in1 = e < a1 || e >= b1;
+          const float2 z = v[out_slot<P>(e)];
+          const float y0 = in0 ? z.x * inv : 0.f;
+          const float y1 = in1 ? z.y * inv : 0.f;
+          w[e] = make_float2(y0, y1);
+          need[u] = in0 || in1;
+          any = any || need[u];
+        });
+        if (__any_sync(0xffffffffu, any)) {
+          float2 old[4];
 #pragma unroll
-      for (int a = 0; a < 32; ++a) {
-        const int n = p + P * out_e<P>(a);
-        const int j0 = 2 * n, j1 = 2 * n + 1;
-        const bool in0 = active && (j0 < NT - j0 ? j0 : NT - j0) < L;
-        const bool in1 = active && (j1 < NT - j1 ? j1 : NT - j1) < L;
-        const float y0 = in0 ? v[a].x * inv : 0.f;
-        const float y1 = in1 ? v[a].y * inv : 0.f;
-        esum = fmaf(y0, y0, esum);
-        esum = fmaf(y1, y1, esum);
-        if (odd) {  // f1plus(-j) += N_i(-j) = -theta(j) s(j)
-          if (in0) f1[base + ((NT - j0) & (NT - 1))] = fa[a] - y0;
-          if (in1) f1[base + (NT - j1)] = fb[a] - y1;
-        } else if (in0 || in1) {  // f1min(j) -= N_i(-j) = theta(j) s(j)
-          reinterpret_cast<float2*>(f1 + base)[n] = make_float2(fa[a] + y0, fb[a] + y1);
+          for (int u = 0; u < 4; ++u) {
+            const int n = p + P * (e0 + u);
+            old[u] = make_float2(0.f, 0.f);
+            if (need[u]) {
+              if (odd) {
+                old[u].x = ft[(NT - 2 * n) & (NT - 1)];
+                old[u].y = ft[NT - 2 * n - 1];
+              } else {
+                old[u] = reinterpret_cast<const float2*>(ft)[n];
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int n = p + P * (e0 + u);
+            if (need[u]) {
+              const float2 y = w[e0 + u];
+              if (odd) {
+                ft[(NT - 2 * n) & (NT - 1)] = old[u].x - y.x;
+                ft[NT - 2 * n - 1] = old[u].y - y.y;
+              } else {
+                reinterpret_cast<float2*>(ft)[n] = make_float2(old[u].x + y.x, old[u].y + y.y);
+              }
+            }
+          }
         }
-        // forward input layout: register e = out_e(a) holds n = p + P e
-        w[out_e<P>(a)] = make_float2(y0, y1);
+      });
+
+      // the lane's share of the energy: four partial sums in a fixed order
+      float eq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int e = 0; e < 32; ++e) {
+        eq[e & 3] = fmaf(w[e].x, w[e].x, eq[e & 3]);
+        eq[e & 3] = fmaf(w[e].y, w[e].y, eq[e & 3]);
       }
+      const float esum = (eq[0] + eq[1]) + (eq[2] + eq[3]);
 
       // 5. forward transform of y
-      group_fft<P, false>(w, gbuf, p, tw);
+      group_fft<NT, false>(w, gbuf, p, s.twl);
 
-      // 6. post-processing: partner Zf_{(M-k) mod M} from lane (P - q) mod P
-      //    (register e'' = 31 - e' there), or for lane 0 its own register
-      //    (32 - e') mod 32
-      float2 part[32];
+      // 6. post-processing for the band bins k = q + P e' < nw: the partner
+      //    Zf_{(M-k) mod M} comes from lane (P - q) mod P of the group
+      //    (its register e'' = 31 - e'), or for lane 0 from its own register
+      //    (32 - e') mod 32.  Y_k = E_k + e^{-2 pi i k/nt} O_k with
+      //    E_k = (Zf_k + conj Zf_{M-k})/2, O_k = (Zf_k - conj Zf_{M-k})/(2i);
+      //    the band spectrum of N_i is -conj(Y_k).
       const int src = (P - p) & (P - 1);
-      static_for<32>([&](auto Rr) {
-        constexpr int r = decltype(Rr)::value;  // e' of the value this lane offers
-        const float2 val = w[out_slot<P>(r)];
-        float2 got;
-        got.x = __shfl_sync(0xffffffffu, val.x, src, P);
-        got.y = __shfl_sync(0xffffffffu, val.y, src, P);
-        constexpr int et = 31 - r;
-        constexpr int own = (r + 1) & 31;
-        part[out_slot<P>(et)] = p != 0 ? got : w[out_slot<P>(own)];
-      });
-      // Y_k = E_k + e^{-2 pi i k/nt} O_k; the band spectrum of N_i is -conj(Y_k)
-      static_for<32>([&](auto Aa) {
-        constexpr int a = decltype(Aa)::value;
-        constexpr int e = out_e<P>(a);
-        const int k = p + P * e;
-        if (active && k < nw) {
-          const float2 Z = w[a];
-          const float2 Zc = make_float2(part[a].x, -part[a].y);
-          const float2 E = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
-          const float2 D = csub(Z, Zc);
-          const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-          const float2 T = rot64<e, false>(cmulc(O, tw.up));
-          st[(size_t)k * ldm + c] = make_float2(-(E.x + T.x), E.y + T.y);
+      static_for<32>([&](auto Ee) {
+        constexpr int e = decltype(Ee)::value;
+        if (e * P < nw) {  // uniform: some lane of every group has k < nw
+          const float2 offer = w[out_slot<P>(31 - e)];
+          float2 got;
+          got.x = __shfl_sync(0xffffffffu, offer.x, src, P);
+          got.y = __shfl_sync(0xffffffffu, offer.y, src, P);
+          const float2 Z = w[out_slot<P>(e)];
+          const float2 pz = p != 0 ? got : w[out_slot<P>((32 - e) & 31)];
+          if (e < ek) {
+            const float2 Zc = make_float2(pz.x, -pz.y);
+            const float2 Ev = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
+            const float2 D = csub(Z, Zc);
+            const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+            const float2 T = rot64<e, false>(cmulc(O, up));
+            col[(p + P * e) * ldm] = make_float2(-(Ev.x + T.x), Ev.y + T.y);
+          }
         }
       });
       if (active && p == 0 && nw == M + 1) {  // Nyquist bin (full band): Y_M = Re Zf_0 - Im Zf_0
-        st[(size_t)M * ldm + c] = make_float2(-(w[0].x - w[0].y), 0.f);
+        col[M * ldm] = make_float2(-(w[0].x - w[0].y), 0.f);
       }
 
       // 7. the trace's energy: lanes combined error-free in FP32, then FP64
@@ -481,20 +596,37 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
     }
     __syncthreads();
 
-    // 8. the block's new band spectra, one coalesced pass
-    const int total = nw << lbt;
-    for (int i = threadIdx.x; i < total; i += kThreads) {
-      const int m = i >> lbt, c = i & (bt - 1);
-      if (c >= ntr) continue;
-      const int t = tb + c;
-      const int f = t / s.ns, k = t - f * s.ns;
-      const float2 val = st[(size_t)m * ldm + c];
+    // 8. the block's new band spectra.  A full block writes whole row
+    //    segments with 16-byte stores (its positions start at a multiple of bt,
+    //    so the segments are 16-byte aligned); a ragged one element by element.
+    if (ntr == bt) {
       if (s.rprec == 0) {
-        s.Nw[(int64_t)m * s.nw_stride + (int64_t)f * s.r_pad + k] = val;
+        store_block_nw(s, st, ldm, bf, k0, bt, lbt);
       } else if (s.rprec == 2) {
-        store_embedding<false>(s, m, f, k, val.x, val.y);
+        store_block_embedding<false, 2>(s, st, ldm, bf, k0, bt, lbt);
+      } else if (s.rprec == 4) {
+        store_block_embedding<true, 3>(s, st, ldm, bf, k0, bt, lbt);
       } else {
-        store_embedding<true>(s, m, f, k, val.x, val.y);
+        store_block_embedding<true, 2>(s, st, ldm, bf, k0, bt, lbt);
+      }
+    } else if (pc < ntr) {
+      const int k = k0 + pc;
+      if (s.rprec == 0) {
+        float2* dst = s.Nw + (int64_t)pm0 * s.nw_stride + (int64_t)bf * s.r_pad + k;
+        const int64_t dstep = (int64_t)pms * s.nw_stride;
+        for (int m = pm0; m < nw; m += pms, dst += dstep) *dst = st[m * ldm + pc];
+      } else {
+        const int64_t kp = 2 * (int64_t)s.r_pad;
+        int64_t e0 = ((int64_t)pm0 * 2 * s.F + 2 * bf) * kp + 2 * k;
+        const int64_t estep = (int64_t)pms * 2 * s.F * kp;
+        for (int m = pm0; m < nw; m += pms, e0 += estep) {
+          const float2 val = st[m * ldm + pc];
+          if (s.rprec == 2) {
+            store_embedding_at<false>(s, e0, val.x, val.y);
+          } else {
+            store_embedding_at<true>(s, e0, val.x, val.y);
+          }
+        }
       }
     }
     __syncthreads();
@@ -534,12 +666,12 @@ bool epi_shape(const SurveyDev& s, int num_sms, EpiShape* out) {
   } else {
     // few traces: one round per block, so that more SMs get blocks
     const int bt2 = kWarps * traces_per_warp<NT>() * 2;
-    if ((s.ncols + bt2 - 1) / bt2 < num_sms) rounds = 1;
+    if (s.F * ((s.ns + bt2 - 1) / bt2) < kCtasPerSm * num_sms) rounds = 1;
   }
   for (; rounds >= 1; --rounds) {
     for (int nbuf = 2; nbuf >= 1; --nbuf) {
       const size_t smem = epi_smem<NT>(s.nw, rounds, nbuf);
-      if (smem <= kSmemMax) {
+      if (smem <= kSmemPerCta) {
         *out = {rounds, nbuf, kWarps * traces_per_warp<NT>() * rounds, smem};
         return true;
       }
@@ -552,15 +684,15 @@ template <int NT>
 cudaError_t launch_nt(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
   EpiShape sh;
   if (!epi_shape<NT>(s, num_sms, &sh)) return cudaErrorNotSupported;
-  const int nblocks = (s.ncols + sh.bt - 1) / sh.bt;
-  const int grid = nblocks < num_sms ? nblocks : num_sms;
+  const int nblocks = s.F * ((s.ns + sh.bt - 1) / sh.bt);
+  const int grid = nblocks < kCtasPerSm * num_sms ? nblocks : kCtasPerSm * num_sms;
   epi_warp_kernel<NT><<<grid, kThreads, sh.smem, st>>>(s, ring, slots, sh.rounds, sh.nbuf);
   return cudaGetLastError();
 }
 
 template <int NT>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(epi_warp_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+  return cudaFuncSetAttribute(epi_warp_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPerCta);
 }
 
 }  // namespace

@@ -403,7 +403,7 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
     const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
     // 1. the block's band spectra, one coalesced pass (bt is a power of two
     //    dividing THREADS, so each thread keeps one trace column c)
-    if (cc < ntr) {
+    if (cc < ntr && !s.pacc) {
       const float2* src = s.S + tb + cc;
       float2* dst = stage + cc * ld;
       int m = mc;
@@ -415,6 +415,16 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
         for (int u = 0; u < 8; ++u) dst[m + u * mstep] = v[u];
       }
       for (; m < s.nw; m += mstep) dst[m] = __ldg(src + (int64_t)m * s.s_stride);
+    } else if (cc < ntr) {
+      // the same, and pmin's band spectrum += S (one thread owns each (m, t))
+      float2* dst = stage + cc * ld;
+      for (int m = mc; m < s.nw; m += mstep) {
+        const int64_t i = (int64_t)m * s.s_stride + tb + cc;
+        const float2 v = __ldg(s.S + i);
+        const float2 a = s.pacc[i];
+        dst[m] = v;
+        s.pacc[i] = make_float2(a.x + v.x, a.y + v.y);
+      }
     }
     if (threadIdx.x < ntr) sL[threadIdx.x] = s.L[tb + threadIdx.x];  // the block's window lengths
     cp_async_wait_all();  // the twiddle table (first block)
@@ -856,8 +866,9 @@ cudaError_t prepare_kernels() {
   return cudaSuccess;
 }
 
-int epilogue_max_pairs(int nt, int nw) {
-  if (epilogue_warp_supports(nt, nw)) return 2;  // one or two rounds of traces per block
+int epilogue_max_pairs(const SurveyDev& s, int num_sms) {
+  if (epilogue_uses_warp(s, num_sms)) return 2;  // one or two rounds of traces per block
+  const int nt = s.nt, nw = s.nw;
   size_t bytes = 0;
   switch (nt) {
 #define MK_FIT(N) \
@@ -908,6 +919,20 @@ __global__ void twiddle_kernel(float2* tw, int nt) {
   tw[e] = make_float2(0.f, 0.f);
 }
 
+// e^{-2 pi i j / nt} for j < nt, formed in FP64 and rounded to FP32.
+__global__ void twiddle_linear_kernel(float2* tw, int nt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nt) return;
+  double sv, cv;
+  sincospi(-2.0 * (double)j / (double)nt, &sv, &cv);
+  tw[j] = make_float2((float)cv, (float)sv);
+}
+
+cudaError_t launch_twiddles_linear(float2* tw, int nt, cudaStream_t st) {
+  twiddle_linear_kernel<<<(nt + 255) / 256, 256, 0, st>>>(tw, nt);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_twiddles(float2* tw, int nt, cudaStream_t st) {
   twiddle_kernel<<<(nt + 255) / 256, 256, 0, st>>>(tw, nt);
   return cudaGetLastError();
@@ -920,8 +945,16 @@ cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// The register epilogue needs enough traces to give every CTA slot a block
+// (one block of up to 8 traces per CTA, two CTAs per SM); with fewer each warp
+// holds a single trace and the shared-memory epilogue, whose 256 threads share
+// a pair of traces, finishes sooner.
+bool epilogue_uses_warp(const SurveyDev& s, int num_sms) {
+  return s.ncols >= 16 * num_sms && epilogue_warp_supports(s.nt, s.nw);
+}
+
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
-  if (epilogue_warp_supports(s.nt, s.nw)) return launch_epilogue_warp(s, ring, slots, st, num_sms);
+  if (epilogue_uses_warp(s, num_sms)) return launch_epilogue_warp(s, ring, slots, st, num_sms);
 #define MK_CALL(N) launch_epi_nt<N>(s, ring, slots, st, num_sms)
   MK_NT_SWITCH(s.nt, MK_CALL)
 #undef MK_CALL

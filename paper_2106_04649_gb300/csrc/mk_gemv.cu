@@ -31,22 +31,11 @@ __device__ __forceinline__ float4 ld_stream(const float4* p) {
   return v;
 }
 
-// S at index i; with pacc also pmin += s_i, kept as a band spectrum (one lane
-// owns each (m, k), so the update is race-free).
-__device__ __forceinline__ void store_s(float2* S, float2* pacc, int64_t i, float2 v) {
-  S[i] = v;
-  if (pacc) {
-    const float2 o = pacc[i];
-    pacc[i] = make_float2(o.x + v.x, o.y + v.y);
-  }
-}
-
 // Rows of RQ float4 (two complex each); lane l owns float4 l, l + 32, ...
 template <int PER>
 __global__ void __launch_bounds__(256)
 gemv_c64_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S,
-                int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows,
-                float2* __restrict__ pacc) {
+                int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -90,15 +79,14 @@ gemv_c64_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, flo
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) store_s(S, pacc, (int64_t)w * s_stride + k, make_float2(c * re, c * im));
+    if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
   }
 }
 
 // Rows longer than the register-resident form: Nw is re-read through L1.
 __global__ void __launch_bounds__(256)
 gemv_c64_long_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S,
-                     int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows,
-                     float2* __restrict__ pacc) {
+                     int ns, int rq, int64_t nw_stride4, int64_t s_stride, float c, int64_t total_rows) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -135,7 +123,7 @@ gemv_c64_long_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw
       re += __shfl_xor_sync(0xffffffffu, re, o);
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
-    if (lane == 0) store_s(S, pacc, (int64_t)w * s_stride + k, make_float2(c * re, c * im));
+    if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
   }
 }
 
@@ -190,7 +178,7 @@ template <int PER>
 __global__ void __launch_bounds__(kBulkThreads, 1)
 gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S, int ns,
                  int rq, int64_t nw_stride4, int64_t s_stride, float c, int nw, int stages,
-                 unsigned* __restrict__ queue, int* __restrict__ err, float2* __restrict__ pacc) {
+                 unsigned* __restrict__ queue, int* __restrict__ err) {
   extern __shared__ __align__(128) float4 ring[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
@@ -305,7 +293,7 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
           re += __shfl_xor_sync(0xffffffffu, re, o);
           im += __shfl_xor_sync(0xffffffffu, im, o);
         }
-        if (lane == 0) store_s(S, pacc, (int64_t)w * s_stride + k, make_float2(c * re, c * im));
+        if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
@@ -352,7 +340,7 @@ cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   cfg.numAttrs = s.pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, gemv_bulk_kernel<PER>, reinterpret_cast<const float4*>(s.R),
                             reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq, s.nw_stride / 2, s.s_stride, s.c,
-                            s.nw, stages, s.counter + 1, s.err, s.pacc);
+                            s.nw, stages, s.counter + 1, s.err);
 }
 
 template <int PER>
@@ -371,7 +359,7 @@ cudaError_t launch_gemv_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   if (grid * 8 > total) grid = (total + 7) / 8;
   gemv_c64_kernel<PER><<<(unsigned)grid, 256, 0, st>>>(
       reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns,
-      s.r_pad / 2, s.nw_stride / 2, s.s_stride, s.c, total, s.pacc);
+      s.r_pad / 2, s.nw_stride / 2, s.s_stride, s.c, total);
   return cudaGetLastError();
 }
 
@@ -417,7 +405,7 @@ cudaError_t launch_gemv(const SurveyDev& s, cudaStream_t st, int num_sms) {
       if (grid * 8 > total) grid = (total + 7) / 8;
       gemv_c64_long_kernel<<<(unsigned)grid, 256, 0, st>>>(
           reinterpret_cast<const float4*>(s.R), reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq,
-          s.nw_stride / 2, s.s_stride, s.c, total, s.pacc);
+          s.nw_stride / 2, s.s_stride, s.c, total);
       return cudaGetLastError();
     }
   }

@@ -49,7 +49,8 @@ struct SurveyDev {
   double* Epart;    // [ncols + 1] per-trace energies
   unsigned* counter;  // [8]: epilogue last-CTA count; GEMV work counter and finished CTAs (1, 2);
                       // tensor-core contraction work counter and finished CTAs (4, 5)
-  const float2* tw;   // [nt] e^{-2 pi i q / nt}
+  const float2* tw;   // [nt] FFT twiddles in the pass-by-pass layout of the shared-memory FFT
+  const float2* twl;  // [nt] e^{-2 pi i j / nt}, j = 0 .. nt-1 (per-lane twiddles of the register FFT)
   int* err;           // device error word (bounded waits that ran out); may be null
   int* iter;          // device iteration index (parity and energy slot; advanced by the epilogue)
   int epi_g;          // epilogue pairs per block: 0 = chosen from shared memory and grid size, else 1, 2 or 4
@@ -59,7 +60,7 @@ struct SurveyDev {
                       // only when no kernel that writes R can precede it on the stream
   float2* pacc;       // null, or [nw][s_stride] running sum of the contraction outputs S of the
                       // Neumann iterations (the band spectrum of pmin, Algorithm 1), added to by
-                      // the F = 1 contraction
+                      // the epilogue when it reads S
 };
 
 // Kernel launchers (return the launch status; the caller checks it).
@@ -77,6 +78,7 @@ cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t ro
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
 cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);
 cudaError_t launch_twiddles(float2* tw, int nt, cudaStream_t st);  // FFT twiddle table of nt entries
+cudaError_t launch_twiddles_linear(float2* tw, int nt, cudaStream_t st);  // e^{-2 pi i j / nt}, j < nt
 bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the per-CTA limit
 // The epilogue with the transforms in registers, one lane group per trace (mk_epi.cu):
 // nt = 64 .. 2048 with a band whose shared stage fits; launch_epilogue uses it
@@ -84,7 +86,10 @@ bool epilogue_fits(int nt, int nw);  // shared memory of the epilogue within the
 bool epilogue_warp_supports(int nt, int nw);
 cudaError_t prepare_epilogue_warp();
 cudaError_t launch_epilogue_warp(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
-int epilogue_max_pairs(int nt, int nw);  // largest pairs-per-block the epilogue's shared memory allows
+// whether launch_epilogue runs the register epilogue for this survey (enough traces
+// to fill the GPU with blocks, a supported shape); otherwise the shared-memory one
+bool epilogue_uses_warp(const SurveyDev& s, int num_sms);
+int epilogue_max_pairs(const SurveyDev& s, int num_sms);  // largest block-size choice of the survey's epilogue
 bool umma_set_bn(UmmaMaps* mp, const SurveyDev& s, int bn);  // N tile of the tensor-core contraction
 int umma_get_bn(const UmmaMaps* mp);
 cudaError_t launch_init(const SurveyDev& s, const float* Gd, cudaStream_t st, int num_sms);

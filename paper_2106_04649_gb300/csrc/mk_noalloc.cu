@@ -118,7 +118,7 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   const size_t tw_bytes = align256((size_t)v.nt * sizeof(float2));
   const size_t slot_bytes = align256((size_t)v.F * sizeof(double));
   const size_t err_bytes = 256;
-  const size_t need = nw_bytes + s_bytes + l_bytes + e_bytes + c_bytes + tw_bytes + slot_bytes + err_bytes + 256;
+  const size_t need = nw_bytes + s_bytes + l_bytes + e_bytes + c_bytes + 2 * tw_bytes + slot_bytes + err_bytes + 256;
   if (need > MK_NOALLOC_SCRATCH_BYTES) {
     char buf[256];
     snprintf(buf, sizeof buf,
@@ -156,8 +156,11 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   off += err_bytes;
   float2* tw = reinterpret_cast<float2*>(base + off);
   off += tw_bytes;
+  float2* twl = reinterpret_cast<float2*>(base + off);
+  off += tw_bytes;
   double* slot = reinterpret_cast<double*>(base + off);
   v.tw = tw;
+  v.twl = twl;
   v.td = nullptr;
   v.scratch = nullptr;
   v.R = static_cast<const float2*>(R);
@@ -173,7 +176,8 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
   // reads before writing (Nw padding, S padding, completion counter).
   if ((e = cudaMemsetAsync(base, 0, off, stream)) != cudaSuccess)
     return set_err(MK_ERR_CUDA, "cudaMemsetAsync failed", cudaGetErrorString(e));
-  if ((e = mk::launch_twiddles(tw, v.nt, stream)) != cudaSuccess)
+  if ((e = mk::launch_twiddles(tw, v.nt, stream)) != cudaSuccess ||
+      (e = mk::launch_twiddles_linear(twl, v.nt, stream)) != cudaSuccess)
     return set_err(MK_ERR_CUDA, "twiddle launch", cudaGetErrorString(e));
   if ((e = mk::launch_windows(v, td, eps_s, stream)) != cudaSuccess)
     return set_err(MK_ERR_CUDA, "window launch", cudaGetErrorString(e));

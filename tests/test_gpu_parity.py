@@ -366,3 +366,38 @@ def test_longest_traces_nt8192(fmax):
         _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"nt=8192 fmax={fmax} iter {i}")
         assert np.max(np.abs(e[0] - hist[i].energy[i]) / hist[i].energy[i]) <= TOL_E
     p.close()
+
+
+def _many_focal(n, nt, dt, F, fmax):
+    s = small_survey(n=n, nt=nt, dt=dt, nfocal=3, fmax_hz=fmax)
+    xs = np.linspace(0.15, 0.85, F) * (n - 1) * s.dx
+    zs = 600.0 + 100.0 * np.linspace(0.0, 1.0, F)
+    s.focal = np.stack([xs, zs], axis=1)
+    return s
+
+
+@pytest.mark.parametrize("nt,dt,fmax,rprec", [(64, 0.016, None, 0), (128, 0.008, 40.0, 0), (256, 0.008, None, 0),
+                                              (512, 0.004, 60.0, 0), (1024, 0.002, 90.0, 0), (2048, 0.001, 150.0, 0),
+                                              (2048, 0.001, 150.0, 4), (512, 0.004, 60.0, 4), (1024, 0.002, 90.0, 1),
+                                              (256, 0.008, None, 2)])
+def test_register_epilogue_shapes(nt, dt, fmax, rprec):
+    # enough traces (33 positions x 80 focal points) for the register epilogue
+    # where the shape fits its shared memory (nt = 64, 512 with a narrow band,
+    # 1024, 2048; the others run the shared-memory epilogue): ragged blocks (33
+    # is no multiple of the block size), full and limited bands, and each output
+    # form (complex FP32 field spectrum; the 2- and 3-part 16-bit embeddings,
+    # BF16 and FP16), per iteration
+    from tests.test_gpu_tensor import dequantised
+    from paper_2106_04649_gb300.api import Plan
+    s = _many_focal(33, nt, dt, 80, fmax)
+    R, td, Gd = survey_inputs(s)
+    Rref = R.astype(np.complex128) if rprec in (0, 4) else dequantised(R, rprec)
+    _, hist = M.run(Rref, Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 3, history=True)
+    p = Plan([desc_for(s, rprec=rprec)])
+    p.load_R(0, R)
+    p.set_Gd_window(0, Gd, td, s.eps)
+    for i in range(3):
+        e = p.iterate(1)
+        _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"nt={nt} rprec={rprec} iter {i}")
+        assert np.max(np.abs(e[0] - hist[i].energy[i]) / hist[i].energy[i]) <= TOL_E
+    p.close()
