@@ -416,14 +416,30 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
       }
       for (; m < s.nw; m += mstep) dst[m] = __ldg(src + (int64_t)m * s.s_stride);
     } else if (cc < ntr) {
-      // the same, and pmin's band spectrum += S (one thread owns each (m, t))
+      // the same, and pmin's band spectrum += S (one thread owns each (m, t)),
+      // eight pairs of loads in flight per thread
       float2* dst = stage + cc * ld;
-      for (int m = mc; m < s.nw; m += mstep) {
-        const int64_t i = (int64_t)m * s.s_stride + tb + cc;
-        const float2 v = __ldg(s.S + i);
-        const float2 a = s.pacc[i];
+      const float2* src = s.S + tb + cc;
+      float2* acc = s.pacc + tb + cc;
+      int m = mc;
+      for (; m + 7 * mstep < s.nw; m += 8 * mstep) {
+        float2 v[8], a[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          v[u] = __ldg(src + (int64_t)(m + u * mstep) * s.s_stride);
+          a[u] = acc[(int64_t)(m + u * mstep) * s.s_stride];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          dst[m + u * mstep] = v[u];
+          acc[(int64_t)(m + u * mstep) * s.s_stride] = make_float2(a[u].x + v[u].x, a[u].y + v[u].y);
+        }
+      }
+      for (; m < s.nw; m += mstep) {
+        const float2 v = __ldg(src + (int64_t)m * s.s_stride);
+        const float2 a = acc[(int64_t)m * s.s_stride];
         dst[m] = v;
-        s.pacc[i] = make_float2(a.x + v.x, a.y + v.y);
+        acc[(int64_t)m * s.s_stride] = make_float2(a.x + v.x, a.y + v.y);
       }
     }
     if (threadIdx.x < ntr) sL[threadIdx.x] = s.L[tb + threadIdx.x];  // the block's window lengths
