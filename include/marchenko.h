@@ -121,7 +121,18 @@ typedef enum {
                                     used when every survey sets it and none
                                     sets MK_FLAG_TIMING                     */
 
-/* One survey.  nsrc == nrec is required (coincident sources/receivers). */
+/* One survey.  nsrc == nrec is required (coincident sources/receivers).
+ *
+ * Shot-row sharding (the paper's multi-GPU split, Implementation section:
+ * each GPU takes its own batch of shots): row_count > 0 makes the plan hold
+ * only the output positions k = row_begin .. row_begin + row_count - 1 of the
+ * survey -- their rows of every R_m, their traces of every field, their mute
+ * windows -- while the field spectrum that the contraction sums over keeps
+ * all nrec positions.  Each iteration then computes the new field spectrum
+ * of the plan's own positions only; the caller completes it from the other
+ * shards between iterations (mk_export_field_spectrum /
+ * mk_import_field_spectrum, e.g. around an all-gather).  row_begin must be a
+ * multiple of 32.  row_count = 0 holds every position (row_begin ignored). */
 typedef struct {
   int32_t nsrc;     /* number of output positions k                          */
   int32_t nrec;     /* number of summed positions r                          */
@@ -132,6 +143,8 @@ typedef struct {
   double fmax_hz;   /* band limit (<= 0: full band)                           */
   int32_t rprec;    /* mk_rprec                                               */
   uint32_t flags;   /* MK_FLAG_*                                              */
+  int32_t row_begin; /* first output position held (shot-row sharding)      */
+  int32_t row_count; /* output positions held; 0: all of them               */
 } mk_desc;
 
 /* Counters of one plan (mk_get_stats). */
@@ -239,8 +252,9 @@ mk_status mk_set_Gd_window(mk_plan_t plan, int32_t survey, const float* Gd, cons
  * series from where it stopped (Algorithm 1, loop over iter; one synthesis,
  * reversal, mute and accumulation per iteration).
  *   energy: NULL, or host double [niter][sum of nfocal over surveys]:
- *           E_i(f) = sum over (k, t) of N_i^2, accumulated in FP64 in a fixed
- *           order (deterministic).  With energy != NULL the call returns
+ *           E_i(f) = sum over (k, t) of N_i^2 (k over the plan's own positions
+ *           for a shot-row shard), FP32 squares summed per trace error-free
+ *           and in FP64 across traces, in a fixed order (deterministic).  With energy != NULL the call returns
  *           after the work is done; with NULL it is asynchronous.
  * Errors: MK_ERR_ARG (niter < 0), MK_ERR_STATE (a survey without G_d),
  *         MK_ERR_CUDA.
@@ -351,6 +365,52 @@ mk_status mk_get_stats(mk_plan_t plan, mk_stats_t* out, int32_t reset);
 #define MK_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float* Gd, const double* td, double eps_s,
                          int32_t niter, float* fields, double* energy, void* cuda_stream);
+
+/*
+ * Shot-row sharding: the exchange of the field spectrum between shards.
+ *
+ * The paper splits the synthesis over GPUs by shots (Implementation
+ * section): every GPU holds its batch of rows of R and contracts the whole
+ * field with them.  A plan made with mk_desc.row_count > 0 holds the output
+ * positions k in [row_begin, row_begin + row_count) of a survey; each
+ * iteration (mk_iterate) computes the next field spectrum at those positions
+ * only.  Before every contraction -- after mk_set_Gd_window and after each
+ * mk_iterate(plan, 1, ...) -- the caller gives every shard the spectrum rows
+ * of all the others: mk_export_field_spectrum on each shard, an all-gather of
+ * the packed buffers (e.g. NCCL), mk_import_field_spectrum of each received
+ * block.  Energies returned by mk_iterate are the sums over the shard's own
+ * positions (the caller adds them up); fetched fields are the shard's own
+ * positions, [nfocal][row_count][nt].  A shard keeps pmin as a band spectrum
+ * during the iterations; G^-, G^+, mk_image, mk_set_fields and
+ * mk_load_R_time need the whole survey and return MK_ERR_UNSUPPORTED.
+ *
+ * Packed layout (bytes = parts * n_w * nfocal * rows * 8, parts = 1 for
+ * complex FP32 R, 2 for the 16-bit and split forms, 3 for the 3-way split):
+ *   complex FP32: complex64 [n_w][nfocal][rows];
+ *   16-bit forms: per part, 16-bit [n_w][2 nfocal][2 rows] (the rows of the
+ *   tensor-core operand), parts one after the other.
+ * Both calls run on the plan's stream, synchronously for host buffers.
+ */
+
+/*
+ * mk_export_field_spectrum - the plan's own rows of the field spectrum
+ * (positions row_begin .. row_begin + row_count - 1, or every position of an
+ * unsharded plan) into dst (host: dst_on_device = 0, device: 1).
+ * Errors: MK_ERR_ARG (null, bytes too small), MK_ERR_STATE (G_d not set),
+ *         MK_ERR_CUDA.
+ */
+mk_status mk_export_field_spectrum(mk_plan_t plan, int32_t survey, void* dst, size_t bytes,
+                                   int32_t dst_on_device);
+
+/*
+ * mk_import_field_spectrum - rows row_begin .. row_begin + row_count - 1 of
+ * the field spectrum from src (packed as above, as another shard exported
+ * them), before the next contraction.
+ * Errors: MK_ERR_ARG (null, rows outside [0, nrec), bytes too small),
+ *         MK_ERR_STATE (G_d not set), MK_ERR_CUDA.
+ */
+mk_status mk_import_field_spectrum(mk_plan_t plan, int32_t survey, const void* src, int32_t row_begin,
+                                   int32_t row_count, size_t bytes, int32_t src_on_device);
 
 /*
  * mk_set_timing - for a plan made with MK_FLAG_TIMING: record the CUDA

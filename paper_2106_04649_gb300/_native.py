@@ -37,6 +37,8 @@ class MkDesc(ctypes.Structure):
         ("fmax_hz", ctypes.c_double),
         ("rprec", ctypes.c_int32),
         ("flags", ctypes.c_uint32),
+        ("row_begin", ctypes.c_int32),
+        ("row_count", ctypes.c_int32),
     ]
 
 
@@ -83,6 +85,9 @@ _SIGS = {
     "mk_load_R_time": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32]),
     "mk_get_tuning": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(MkTuning)]),
     "mk_set_timing": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "mk_export_field_spectrum": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_size_t, ctypes.c_int32]),
+    "mk_import_field_spectrum": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_size_t, ctypes.c_int32]),
     "mk_run_noalloc": (ctypes.c_int, [ctypes.POINTER(MkDesc), _P, _P, _P, ctypes.c_double, ctypes.c_int32, _P, _P,
                                       _P]),
 }

@@ -28,6 +28,8 @@ class Desc:
     fmax_hz: float = 0.0
     rprec: int = N.MK_R_C64
     flags: int = 0
+    row_begin: int = 0   # shot-row sharding: first output position held
+    row_count: int = 0   # output positions held (0: all)
 
     @property
     def nw(self) -> int:
@@ -143,6 +145,30 @@ class Plan:
         else:
             a, ptr = _ptr_host(fields, np.float32)
             B.mk_set_fields(self.handle, survey, mask, ptr, a.nbytes, iteration, False)
+
+    # -- shot-row sharding ------------------------------------------------------
+    def spectrum_bytes(self, survey: int, rows: int) -> int:
+        """Bytes of `rows` packed rows of the survey's field spectrum."""
+        d = self.descs[survey]
+        parts = 1 if d.rprec == N.MK_R_C64 else (3 if d.rprec == N.MK_R_SPLIT3_BF16 else 2)
+        return parts * d.nw * d.nfocal * rows * 8
+
+    def export_spectrum(self, survey: int, out: torch.Tensor | None = None) -> torch.Tensor:
+        """The plan's own rows of the field spectrum, packed, into a uint8 CUDA tensor."""
+        d = self.descs[survey]
+        rows = d.row_count if d.row_count > 0 else d.nsrc
+        n = self.spectrum_bytes(survey, rows)
+        if out is None:
+            out = torch.empty(n, dtype=torch.uint8, device=self.device)
+        assert out.is_cuda and out.is_contiguous() and out.numel() * out.element_size() >= n
+        B.mk_export_field_spectrum(self.handle, survey, out.data_ptr(), n, True)
+        return out
+
+    def import_spectrum(self, survey: int, buf: torch.Tensor, row_begin: int, row_count: int) -> None:
+        """Rows row_begin .. row_begin + row_count - 1 of the field spectrum from a packed CUDA buffer."""
+        n = self.spectrum_bytes(survey, row_count)
+        assert buf.is_cuda and buf.is_contiguous() and buf.numel() * buf.element_size() >= n
+        B.mk_import_field_spectrum(self.handle, survey, buf.data_ptr(), row_begin, row_count, n, True)
 
     def tuning(self, survey: int) -> dict:
         """Kernel shapes of a survey (timed at its first set_Gd_window with MK_FLAG_AUTOTUNE)."""

@@ -91,6 +91,16 @@ def mk_image(plan: int, survey: int, image: int, dst_on_device: bool) -> None:
     _check(N.load().mk_image(plan, survey, image, int(dst_on_device)), plan)
 
 
+def mk_export_field_spectrum(plan: int, survey: int, dst: int, nbytes: int, dst_on_device: bool) -> None:
+    _check(N.load().mk_export_field_spectrum(plan, survey, dst, nbytes, int(dst_on_device)), plan)
+
+
+def mk_import_field_spectrum(plan: int, survey: int, src: int, row_begin: int, row_count: int, nbytes: int,
+                             src_on_device: bool) -> None:
+    _check(N.load().mk_import_field_spectrum(plan, survey, src, row_begin, row_count, nbytes, int(src_on_device)),
+           plan)
+
+
 def mk_get_stats(plan: int, reset: bool = False) -> dict:
     st = N.MkStats()
     _check(N.load().mk_get_stats(plan, ctypes.byref(st), int(reset)), plan)

@@ -127,21 +127,31 @@ mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: streaming R from the host needs complex FP32 R", i);
   if ((int64_t)d.nsrc * d.nfocal > (int64_t)1 << 30)
     return fail(p, MK_ERR_ARG, "survey %d: nsrc * nfocal too large", i);
+  if (d.row_count < 0 || (d.row_count > 0 && (d.row_begin < 0 || d.row_begin % 32 != 0 ||
+                                               d.row_begin + d.row_count > d.nsrc)))
+    return fail(p, MK_ERR_ARG, "survey %d: rows [%d, %d) must lie in [0, %d) and start at a multiple of 32", i,
+                d.row_begin, d.row_begin + d.row_count, d.nsrc);
+  if (d.row_count > 0 && (d.flags & MK_FLAG_STREAM_R))
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: a shot-row shard keeps its R resident", i);
   return MK_OK;
 }
+
+bool is_shard(const mk_desc& d) { return d.row_count > 0 && d.row_count < d.nsrc; }
 
 // Sizes and strides of one survey; carves the workspace when base != nullptr.
 size_t layout(Survey& sv, char* base) {
   const mk_desc& d = sv.d;
   mk::SurveyDev& v = sv.dev;
-  v.ns = d.nsrc;
+  v.ns = is_shard(d) ? d.row_count : d.nsrc;
+  v.nr = d.nrec;
+  v.row0 = is_shard(d) ? d.row_begin : 0;
   v.nt = d.nt;
   v.F = d.nfocal;
   v.nw = band_bins(d);
   // rows of R padded for aligned loads: to 32 complex values for the tensor-core and
   // SIMT GEMM tiles and for the host layout of streamed R; a GEMV-only survey (complex
   // FP32, one focal point, resident R) needs 16-byte rows only, an even count
-  const bool gemv_only = d.rprec == MK_R_C64 && d.nfocal == 1 && !(d.flags & MK_FLAG_STREAM_R);
+  const bool gemv_only = d.rprec == MK_R_C64 && d.nfocal == 1 && !(d.flags & MK_FLAG_STREAM_R) && !is_shard(d);
   v.r_pad = gemv_only ? (d.nrec + 1) / 2 * 2 : (d.nrec + 31) / 32 * 32;
   v.ncols = v.ns * v.F;
   v.s_stride = ((int64_t)v.ncols + 1 + 3) / 4 * 4;
@@ -198,8 +208,11 @@ size_t layout(Survey& sv, char* base) {
   // streamed R) accumulates pmin as a band spectrum during the iterations
   // (Algorithm 1 adds every synthesis result to pmin): n_w * ns complex values,
   // far less than R, and no extra contraction when pmin or G is fetched
+  // A shot-row shard keeps it too: its fetch-time synthesis would need the
+  // field spectrum of every shard.
   const bool gemv = d.rprec == MK_R_C64 && d.nfocal == 1;
-  sv.pacc = gemv ? reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2))) : nullptr;
+  sv.pacc = gemv || is_shard(d) ? reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)))
+                                : nullptr;
   v.fN = reinterpret_cast<float*>(take(field));
   v.f1p = reinterpret_cast<float*>(take(field));
   v.f1m = reinterpret_cast<float*>(take(field));
@@ -473,6 +486,14 @@ mk_status materialize_up_down(mk_plan_t p, Survey& sv, uint32_t mask) {
 mk_status materialize(mk_plan_t p, Survey& sv, uint32_t mask) {
   mk::SurveyDev& v = sv.dev;
   const bool need_pmin = mask & (MK_F_PMIN | MK_F_G);
+  if (is_shard(sv.d)) {
+    // a shard holds only its own positions of every field: what needs a
+    // synthesis of a whole field needs the other shards
+    if (mask & (MK_F_GMINUS | MK_F_GPLUS))
+      return fail(p, MK_ERR_UNSUPPORTED, "G^- and G^+ of a shot-row shard need the fields of every shard");
+    if (need_pmin && sv.iter > 0 && !sv.pacc_valid && !sv.derived_valid)
+      return fail(p, MK_ERR_UNSUPPORTED, "pmin of a shot-row shard whose R changed during the series");
+  }
   const bool need_f2p = need_pmin || (mask & MK_F_F2P);
   const bool need_n = need_f2p || (mask & (MK_F_N | MK_F_GMINUS | MK_F_GPLUS));
   if (need_n && !sv.n_in_field) {
@@ -656,13 +677,13 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
   if (v.rprec == MK_R_C64) {
     float2* dst = const_cast<float2*>(v.R) + row0 * v.r_pad;
     if (direct || pinned) {
-      MK_CUDA(p, mk::launch_load_rows(src, dst, rows, v.ns, v.r_pad, p->stream, max_blocks));
+      MK_CUDA(p, mk::launch_load_rows(src, dst, rows, v.nr, v.r_pad, p->stream, max_blocks));
       p->stats.launches++;
       p->stats.other_launches++;
     } else {
       // pageable host memory: the CUDA driver stages the copy
-      MK_CUDA(p, cudaMemcpy2DAsync(dst, (size_t)v.r_pad * sizeof(float2), Rw, (size_t)v.ns * sizeof(float2),
-                                   (size_t)v.ns * sizeof(float2), (size_t)rows, cudaMemcpyHostToDevice,
+      MK_CUDA(p, cudaMemcpy2DAsync(dst, (size_t)v.r_pad * sizeof(float2), Rw, (size_t)v.nr * sizeof(float2),
+                                   (size_t)v.nr * sizeof(float2), (size_t)rows, cudaMemcpyHostToDevice,
                                    p->stream));
     }
   } else if (direct || pinned) {
@@ -672,12 +693,12 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
   } else {
     // pageable host memory into 16-bit storage: chunks through the scratch field
     const size_t scratch_bytes = (size_t)v.F * v.ns * v.nt * sizeof(float);
-    int64_t chunk = (int64_t)(scratch_bytes / ((size_t)v.ns * sizeof(float2)));
+    int64_t chunk = (int64_t)(scratch_bytes / ((size_t)v.nr * sizeof(float2)));
     if (chunk < 1) return fail(p, MK_ERR_UNSUPPORTED, "pageable R rows larger than the staging area");
     for (int64_t r = 0; r < rows; r += chunk) {
       const int64_t n = rows - r < chunk ? rows - r : chunk;
-      MK_CUDA(p, cudaMemcpyAsync(v.scratch, static_cast<const float2*>(Rw) + r * v.ns,
-                                 (size_t)n * v.ns * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+      MK_CUDA(p, cudaMemcpyAsync(v.scratch, static_cast<const float2*>(Rw) + r * v.nr,
+                                 (size_t)n * v.nr * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
       MK_CUDA(p, mk::launch_load_rows_q(reinterpret_cast<const float2*>(v.scratch), v, row0 + r, n, p->stream,
                                         p->num_sms * 16));
       p->stats.launches++;
@@ -705,6 +726,7 @@ mk_status mk_load_R_time(mk_plan_t p, int32_t survey, const float* Rt, int32_t s
   if ((st = ensure_device(p)) != MK_OK) return st;
   const mk::SurveyDev& v = sv->dev;
   if (sv->stream_r) return fail(p, MK_ERR_STATE, "survey %d streams R from the host: use mk_attach_R_host", survey);
+  if (is_shard(sv->d)) return fail(p, MK_ERR_UNSUPPORTED, "survey %d is a shot-row shard: load its R rows with mk_load_R", survey);
   if (!Rt) return fail(p, MK_ERR_ARG, "null R pointer");
   const float* src = Rt;
   bool direct = src_on_device != 0;
@@ -1036,6 +1058,8 @@ mk_status mk_set_fields(mk_plan_t p, int32_t survey, uint32_t mask, const float*
     return fail(p, MK_ERR_ARG, "field mask 0x%x invalid: N, f1plus and f1min are required, G cannot be set", mask);
   if (iteration < 0) return fail(p, MK_ERR_ARG, "iteration < 0");
   if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
+  if (is_shard(sv->d))
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d is a shot-row shard: its pmin cannot be resumed from fields", survey);
   const mk::SurveyDev& v = sv->dev;
   const size_t field = (size_t)v.F * v.ns * v.nt;
   const size_t need = (size_t)__builtin_popcount(mask) * field * sizeof(float);
@@ -1081,6 +1105,78 @@ mk_status mk_image(mk_plan_t p, int32_t survey, double* image, int32_t dst_on_de
     if ((st = check_device_errors(p)) != MK_OK) return st;
   }
   return MK_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Rows [r0, r0 + rc) of the field spectrum operand as a packed buffer: one
+// strided 2-D copy per part.  Complex FP32 Nw [nw][F][r_pad]: rows of rc
+// complex values; 16-bit embedding parts [nw][2F][2 r_pad]: rows of 2 rc
+// 16-bit values.  Packed layout [part][nw][F or 2F][row values], part after
+// part; bytes = parts * nw * F * rc * 8 in both cases.
+mk_status field_spectrum_copy(mk_plan_t p, Survey& sv, void* packed, int r0, int rc, size_t bytes, int on_device,
+                              bool out) {
+  const mk::SurveyDev& v = sv.dev;
+  const int parts = v.rprec == MK_R_C64 ? 1 : (v.rprec == MK_R_SPLIT3_BF16 ? 3 : 2);
+  const size_t need = (size_t)parts * v.nw * v.F * rc * 8;
+  if (bytes < need) return fail(p, MK_ERR_ARG, "field spectrum rows need %zu bytes, %zu given", need, bytes);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+  char* pk = static_cast<char*>(packed);
+  for (int q = 0; q < parts; ++q) {
+    size_t pitch, width, height;
+    char* op;
+    if (v.rprec == MK_R_C64) {
+      pitch = (size_t)v.r_pad * sizeof(float2);
+      width = (size_t)rc * sizeof(float2);
+      height = (size_t)v.nw * v.F;
+      op = reinterpret_cast<char*>(v.Nw) + (size_t)r0 * sizeof(float2);
+    } else {
+      void* part = q == 0 ? v.Bq0 : (q == 1 ? v.Bq1 : v.Bq2);
+      pitch = (size_t)v.r_pad * 4;
+      width = (size_t)rc * 4;
+      height = (size_t)v.nw * 2 * v.F;
+      op = static_cast<char*>(part) + (size_t)r0 * 4;
+    }
+    char* pq = pk + (size_t)q * width * height;
+    if (out) {
+      MK_CUDA(p, cudaMemcpy2DAsync(pq, width, op, pitch, width, height, kind, p->stream));
+    } else {
+      MK_CUDA(p, cudaMemcpy2DAsync(op, pitch, pq, width, width, height, kind, p->stream));
+    }
+  }
+  if (!on_device) MK_CUDA(p, cudaStreamSynchronize(p->stream));
+  return MK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mk_status mk_export_field_spectrum(mk_plan_t p, int32_t survey, void* dst, size_t bytes, int32_t dst_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!dst) return fail(p, MK_ERR_ARG, "null output pointer");
+  if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
+  return field_spectrum_copy(p, *sv, dst, sv->dev.row0, sv->dev.ns, bytes, dst_on_device, true);
+}
+
+mk_status mk_import_field_spectrum(mk_plan_t p, int32_t survey, const void* src, int32_t row_begin,
+                                   int32_t row_count, size_t bytes, int32_t src_on_device) {
+  Survey* sv = nullptr;
+  mk_status st = get_survey(p, survey, &sv);
+  if (st != MK_OK) return st;
+  p->err[0] = 0;
+  if ((st = ensure_device(p)) != MK_OK) return st;
+  if (!src) return fail(p, MK_ERR_ARG, "null input pointer");
+  if (!sv->ready) return fail(p, MK_ERR_STATE, "survey %d has no G_d (call mk_set_Gd_window)", survey);
+  if (row_begin < 0 || row_count < 1 || row_begin + row_count > sv->dev.nr)
+    return fail(p, MK_ERR_ARG, "rows [%d, %d) outside [0, %d)", row_begin, row_begin + row_count, sv->dev.nr);
+  return field_spectrum_copy(p, *sv, const_cast<void*>(src), row_begin, row_count, bytes, src_on_device, false);
 }
 
 mk_status mk_set_timing(mk_plan_t p, int32_t stride, int32_t reserve_pairs) {

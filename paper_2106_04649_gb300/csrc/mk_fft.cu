@@ -344,7 +344,7 @@ __device__ __forceinline__ void stage_store(const SurveyDev& s, const float2* st
                                             int mc, int mstep) {
   if (cc >= ntr) return;
   const int t = tb + cc;
-  const int f = t / s.ns, k = t - f * s.ns;
+  const int f = t / s.ns, k = t - f * s.ns + s.row0;  // k on the field spectrum's r axis
   const float2* row = stage + cc * ld;
   if (s.rprec == 0) {
     float2* dst = s.Nw + (int64_t)f * s.r_pad + k;

@@ -14,7 +14,9 @@ namespace mk {
 // [nw][F][r_pad]: element (m, f, r) at m * nw_stride + f * r_pad + r, the
 // padding r >= ns zero.
 struct SurveyDev {
-  int ns;          // positions (nsrc == nrec)
+  int ns;          // output positions held (all nsrc, or the rows of a shot-row shard)
+  int nr;          // summed positions (nrec): the r axis of R rows and of the field spectrum
+  int row0;        // position of output row 0 on the r axis (first row of a shard, else 0)
   int nt;          // samples
   int F;           // focal points
   int nw;          // kept frequency bins

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) load_rows_q_kernel(const float2* __restri
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int nrec = s.ns;
+  const int nrec = s.nr;
   for (int64_t row = warp; row < rows; row += nwarps) {
     const float2* sr = src + row * nrec;
     const int64_t o = (row0 + row) * s.r_pad;  // in complex elements

@@ -87,12 +87,16 @@ extern "C" mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float
     return set_err(MK_ERR_UNSUPPORTED, "nt must be a power of two in [32, 8192]");
   if (!(d->dt > 0.0) || !(d->dx > 0.0)) return set_err(MK_ERR_ARG, "dt and dx must be > 0");
   if (d->rprec != MK_R_C64) return set_err(MK_ERR_UNSUPPORTED, "only complex FP32 R (MK_R_C64)");
+  if (d->row_count != 0 && !(d->row_begin == 0 && d->row_count == d->nsrc))
+    return set_err(MK_ERR_UNSUPPORTED, "shot-row shards need a plan (mk_plan)");
   if ((int64_t)d->nsrc * d->nfocal > (int64_t)1 << 30) return set_err(MK_ERR_ARG, "nsrc * nfocal too large");
 
   // sizes, strides and the carving of the scratch array
   mk::SurveyDev v;
   memset(&v, 0, sizeof v);
   v.ns = d->nsrc;
+  v.nr = d->nrec;
+  v.row0 = 0;
   v.nt = d->nt;
   v.F = d->nfocal;
   if (!(d->fmax_hz > 0.0)) {

@@ -42,8 +42,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_desc_layout_matches_c():
     from paper_2106_04649_gb300 import _native as N
-    # int32 x4, double x3, int32, uint32 -> 48 bytes with natural alignment
-    assert ctypes.sizeof(N.MkDesc) == 48
+    # int32 x4, double x3, int32, uint32, int32 x2 -> 56 bytes with natural alignment
+    assert ctypes.sizeof(N.MkDesc) == 56
     assert ctypes.sizeof(N.MkStats) == 64
     assert ctypes.sizeof(N.MkTuning) == 24
 

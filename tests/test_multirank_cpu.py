@@ -1,4 +1,5 @@
-"""Multi-rank host logic on CPU (gloo, world size 2): focal-point sharding.
+"""Multi-rank host logic on CPU (gloo, world size 2): focal-point sharding
+and shot-row sharding.
 
 Focal points are independent Neumann series over the same R, so the N > 1
 path gives each rank its own focal points (no collective on the data path).
@@ -82,3 +83,84 @@ def test_focal_shard_partition():
     parts = [S.focal_shard(focal, 4, r) for r in range(4)]
     assert sum(p.shape[0] for p in parts) == 10
     assert sorted(np.concatenate(parts)[:, 0].tolist()) == sorted(focal[:, 0].tolist())
+
+
+# --------------------------------------------------------------------------
+# shot-row sharding: each rank holds a block of output positions (rows of R)
+# and all-gathers the new field between iterations (the paper's multi-GPU
+# split by shots, Implementation section)
+# --------------------------------------------------------------------------
+
+def _rows_worker(rank, world, port, out_path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import synthetic as S
+    from oracle import marchenko as M
+    from tests.conftest import small_survey
+    s = small_survey(n=21, nt=64, nfocal=2)
+    bounds = [(0, 11), (11, 21)]
+    a, b = bounds[rank]
+    R = S.reflection_band(s)
+    td = S.survey_td(s)
+    Gd = S.gd_traces(s, td, np.float64)
+    c = s.dx * s.dt
+    theta = M.theta_mask(td[:, a:b], s.eps, s.nt, s.dt)
+    # the rank's rows of every field; the whole current N after each gather
+    N_full = M.reverse_time(Gd)
+    f1plus = N_full[:, a:b].copy()
+    f2p = N_full[:, a:b].copy()
+    f1min = np.zeros_like(f1plus)
+    pmin = np.zeros_like(f1plus)
+    energy = []
+    for i in range(5):
+        s_rows = M.synthesis(R[:, a:b, :], N_full, c)      # Eq. (1) with this rank's rows of R
+        pmin = pmin + s_rows
+        Ni = -M.reverse_time(s_rows) * theta
+        f2p = f2p + Ni
+        if i % 2 == 0:
+            f1min = f1min - M.reverse_time(Ni)
+        else:
+            f1plus = f1plus + Ni
+        e = torch.from_numpy(np.sum(Ni * Ni, axis=(1, 2)))
+        dist.all_reduce(e)                                 # energies add up over the ranks
+        energy.append(e.numpy())
+        # all-gather of the new field (gloo wants equal sizes: pad to the
+        # largest shard, trim after)
+        rmax = max(hi - lo for lo, hi in bounds)
+        mine = torch.zeros((Ni.shape[0], rmax, Ni.shape[2]), dtype=torch.float64)
+        mine[:, : b - a] = torch.from_numpy(Ni)
+        parts = [torch.zeros_like(mine) for _ in bounds]
+        dist.all_gather(parts, mine)
+        N_full = np.concatenate([p.numpy()[:, : hi - lo] for p, (lo, hi) in zip(parts, bounds)], axis=1)
+    rmax = max(hi - lo for lo, hi in bounds)
+    mine = torch.zeros((4, 2, rmax, s.nt), dtype=torch.float64)
+    mine[:, :, : b - a] = torch.from_numpy(np.stack([f1plus, f1min, f2p, pmin]))
+    gathered = [torch.zeros_like(mine) for _ in bounds]
+    dist.all_gather(gathered, mine)
+    if rank == 0:
+        np.savez(out_path, N=N_full, E=np.array(energy),
+                 **{f"p{r}": g.numpy()[:, :, : hi - lo] for r, (g, (lo, hi)) in enumerate(zip(gathered, bounds))})
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_shot_row_sharding_equals_unsharded(tmp_path):
+    import synthetic as S
+    from oracle import marchenko as M
+    from tests.conftest import small_survey
+    out = str(tmp_path / "rows.npz")
+    mp.start_processes(_rows_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
+    d = np.load(out)
+    s = small_survey(n=21, nt=64, nfocal=2)
+    R = S.reflection_band(s)
+    td = S.survey_td(s)
+    Gd = S.gd_traces(s, td, np.float64)
+    st = M.run(R, Gd, td, s.eps, s.dt, s.dx, 5)
+    fields = np.concatenate([d["p0"], d["p1"]], axis=2)   # [4][F][n][nt]
+    for got, ref in zip(fields, (st.f1plus, st.f1min, st.f2p, st.pmin)):
+        assert np.allclose(got, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+    assert np.allclose(d["N"], st.N, rtol=0, atol=1e-12 * np.max(np.abs(st.N)))
+    assert np.allclose(d["E"], np.array(st.energy), rtol=1e-12, atol=0)
