@@ -123,10 +123,15 @@ class Plan:
         B.mk_image(self.handle, survey, out.ctypes.data, False)
         return out
 
+    def rows(self, survey: int) -> int:
+        """Output positions the plan holds for a survey (a shard's rows, else nsrc)."""
+        d = self.descs[survey]
+        return d.row_count if 0 < d.row_count < d.nsrc else d.nsrc
+
     def fetch_fields(self, survey: int, mask: int = 0x3F, out=None):
         d = self.descs[survey]
         nf = bin(mask).count("1")
-        shape = (nf, d.nfocal, d.nsrc, d.nt)
+        shape = (nf, d.nfocal, self.rows(survey), d.nt)
         if out is None:
             out = np.empty(shape, dtype=np.float32)
         if isinstance(out, torch.Tensor):
@@ -155,9 +160,7 @@ class Plan:
 
     def export_spectrum(self, survey: int, out: torch.Tensor | None = None) -> torch.Tensor:
         """The plan's own rows of the field spectrum, packed, into a uint8 CUDA tensor."""
-        d = self.descs[survey]
-        rows = d.row_count if d.row_count > 0 else d.nsrc
-        n = self.spectrum_bytes(survey, rows)
+        n = self.spectrum_bytes(survey, self.rows(survey))
         if out is None:
             out = torch.empty(n, dtype=torch.uint8, device=self.device)
         assert out.is_cuda and out.is_contiguous() and out.numel() * out.element_size() >= n
