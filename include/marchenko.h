@@ -86,7 +86,12 @@ typedef enum {
   MK_R_CBF16 = 1,      /* complex BF16 (tensor-core contraction)              */
   MK_R_CF16 = 2,       /* complex FP16 (tensor-core contraction)              */
   MK_R_SPLIT_BF16 = 3, /* BF16 hi + BF16 lo parts (3-product tensor-core form) */
-  MK_R_SPLIT3_BF16 = 4 /* BF16 hi + mid + lo parts (6-product form, FP32-like)  */
+  MK_R_SPLIT3_BF16 = 4, /* BF16 hi + mid + lo parts (6-product form, FP32-like) */
+  MK_R_SPLIT_F16 = 5    /* FP16 hi + lo parts of R and of the field, each scaled by a
+                           power of two (R per frequency, the field per frequency
+                           and focal point) into FP16's normal range: about 22
+                           significant bits per operand with 3 products (hh, hl,
+                           lh); loaded with mk_load_R only                    */
 } mk_rprec;
 
 /* Field selection bits for mk_fetch_fields (output order = bit order). */
@@ -385,8 +390,9 @@ mk_status mk_run_noalloc(const mk_desc* d, const void* R, const float* Gd, const
  * mk_load_R_time need the whole survey and return MK_ERR_UNSUPPORTED.
  *
  * Packed layout (bytes = parts * n_w * nfocal * rows * 8, parts = 1 for
- * complex FP32 R, 2 for the 16-bit and split forms, 3 for the 3-way split):
- *   complex FP32: complex64 [n_w][nfocal][rows];
+ * complex FP32 R and the scaled FP16 split, 2 for the other 16-bit and split
+ * forms, 3 for the 3-way split):
+ *   complex FP32 and scaled FP16 split: complex64 [n_w][nfocal][rows];
  *   16-bit forms: per part, 16-bit [n_w][2 nfocal][2 rows] (the rows of the
  *   tensor-core operand), parts one after the other.
  * Both calls run on the plan's stream, synchronously for host buffers.

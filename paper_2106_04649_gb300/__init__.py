@@ -23,6 +23,7 @@ from ._native import (  # noqa: F401
     MK_R_CF16,
     MK_R_SPLIT_BF16,
     MK_R_SPLIT3_BF16,
+    MK_R_SPLIT_F16,
 )
 
 

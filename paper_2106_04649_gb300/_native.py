@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libmarchenk
 MK_OK, MK_ERR_ARG, MK_ERR_STATE, MK_ERR_OOM, MK_ERR_CUDA, MK_ERR_TIMEOUT, MK_ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = ["MK_OK", "MK_ERR_ARG", "MK_ERR_STATE", "MK_ERR_OOM", "MK_ERR_CUDA", "MK_ERR_TIMEOUT",
                 "MK_ERR_UNSUPPORTED"]
-MK_R_C64, MK_R_CBF16, MK_R_CF16, MK_R_SPLIT_BF16, MK_R_SPLIT3_BF16 = range(5)
+MK_R_C64, MK_R_CBF16, MK_R_CF16, MK_R_SPLIT_BF16, MK_R_SPLIT3_BF16, MK_R_SPLIT_F16 = range(6)
 MK_F_N, MK_F_F1P, MK_F_F1M, MK_F_F2P, MK_F_PMIN, MK_F_G, MK_F_GMINUS, MK_F_GPLUS = (1 << i for i in range(8))
 MK_F_ALL = 0xFF
 MK_FLAG_TIMING = 1

@@ -155,7 +155,7 @@ class Plan:
     def spectrum_bytes(self, survey: int, rows: int) -> int:
         """Bytes of `rows` packed rows of the survey's field spectrum."""
         d = self.descs[survey]
-        parts = 1 if d.rprec == N.MK_R_C64 else (3 if d.rprec == N.MK_R_SPLIT3_BF16 else 2)
+        parts = 1 if d.rprec in (N.MK_R_C64, N.MK_R_SPLIT_F16) else (3 if d.rprec == N.MK_R_SPLIT3_BF16 else 2)
         return parts * d.nw * d.nfocal * rows * 8
 
     def export_spectrum(self, survey: int, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -121,7 +121,7 @@ mk_status check_desc(mk_plan_t p, const mk_desc& d, int i) {
   if (!mk::epilogue_fits(d.nt, band_bins(d)))
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: nt=%d with %d kept bins exceeds the epilogue's shared memory", i,
                 d.nt, band_bins(d));
-  if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT3_BF16)
+  if (d.rprec < MK_R_C64 || d.rprec > MK_R_SPLIT_F16)
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: unknown R storage precision %d", i, d.rprec);
   if ((d.flags & MK_FLAG_STREAM_R) && d.rprec != MK_R_C64)
     return fail(p, MK_ERR_UNSUPPORTED, "survey %d: streaming R from the host needs complex FP32 R", i);
@@ -163,6 +163,7 @@ size_t layout(Survey& sv, char* base) {
   v.epi_g = 0;
   v.pdl = 0;
   v.pacc = nullptr;
+  v.rsc = v.nsc = nullptr;
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
     char* ptr = base ? base + off : nullptr;
@@ -202,6 +203,13 @@ size_t layout(Survey& sv, char* base) {
     v.Bq0 = take(bq);
     v.Bq1 = take(bq);
     v.Bq2 = d.rprec == MK_R_SPLIT3_BF16 ? take(bq) : nullptr;
+    if (d.rprec == MK_R_SPLIT_F16) {
+      // the epilogue writes the FP32 field spectrum; each contraction scales and
+      // splits it into the embedding (powers of two per frequency and focal point)
+      v.Nw = reinterpret_cast<float2*>(take((size_t)v.nw * v.nw_stride * sizeof(float2)));
+      v.rsc = reinterpret_cast<float*>(take((size_t)v.nw * sizeof(float)));
+      v.nsc = reinterpret_cast<float*>(take((size_t)v.nw * v.F * sizeof(float)));
+    }
   }
   v.S = reinterpret_cast<float2*>(take((size_t)v.nw * v.s_stride * sizeof(float2)));
   // a survey contracted by the GEMV (complex FP32, one focal point, resident or
@@ -687,6 +695,13 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
                                    p->stream));
     }
   } else if (direct || pinned) {
+    if (v.rprec == MK_R_SPLIT_F16) {  // the frequencies' scales first
+      MK_CUDA(p, cudaMemsetAsync(v.rsc + w_begin, 0, (size_t)w_count * sizeof(float), p->stream));
+      MK_CUDA(p, mk::launch_r_amax(src, v, row0, rows, p->stream, max_blocks));
+      MK_CUDA(p, mk::launch_r_scale(v, w_begin, w_count, p->stream));
+      p->stats.launches += 2;
+      p->stats.other_launches += 2;
+    }
     MK_CUDA(p, mk::launch_load_rows_q(src, v, row0, rows, p->stream, max_blocks));
     p->stats.launches++;
     p->stats.other_launches++;
@@ -695,6 +710,17 @@ mk_status mk_load_R(mk_plan_t p, int32_t survey, const void* Rw, int32_t w_begin
     const size_t scratch_bytes = (size_t)v.F * v.ns * v.nt * sizeof(float);
     int64_t chunk = (int64_t)(scratch_bytes / ((size_t)v.nr * sizeof(float2)));
     if (chunk < 1) return fail(p, MK_ERR_UNSUPPORTED, "pageable R rows larger than the staging area");
+    if (v.rprec == MK_R_SPLIT_F16) {  // the frequencies' scales: one staged pass before the conversion
+      MK_CUDA(p, cudaMemsetAsync(v.rsc + w_begin, 0, (size_t)w_count * sizeof(float), p->stream));
+      for (int64_t r = 0; r < rows; r += chunk) {
+        const int64_t n = rows - r < chunk ? rows - r : chunk;
+        MK_CUDA(p, cudaMemcpyAsync(v.scratch, static_cast<const float2*>(Rw) + r * v.nr,
+                                   (size_t)n * v.nr * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+        MK_CUDA(p, mk::launch_r_amax(reinterpret_cast<const float2*>(v.scratch), v, row0 + r, n, p->stream,
+                                     p->num_sms * 16));
+      }
+      MK_CUDA(p, mk::launch_r_scale(v, w_begin, w_count, p->stream));
+    }
     for (int64_t r = 0; r < rows; r += chunk) {
       const int64_t n = rows - r < chunk ? rows - r : chunk;
       MK_CUDA(p, cudaMemcpyAsync(v.scratch, static_cast<const float2*>(Rw) + r * v.nr,
@@ -727,6 +753,8 @@ mk_status mk_load_R_time(mk_plan_t p, int32_t survey, const float* Rt, int32_t s
   const mk::SurveyDev& v = sv->dev;
   if (sv->stream_r) return fail(p, MK_ERR_STATE, "survey %d streams R from the host: use mk_attach_R_host", survey);
   if (is_shard(sv->d)) return fail(p, MK_ERR_UNSUPPORTED, "survey %d is a shot-row shard: load its R rows with mk_load_R", survey);
+  if (sv->d.rprec == MK_R_SPLIT_F16)
+    return fail(p, MK_ERR_UNSUPPORTED, "survey %d: the scaled FP16 split loads its band spectra with mk_load_R", survey);
   if (!Rt) return fail(p, MK_ERR_ARG, "null R pointer");
   const float* src = Rt;
   bool direct = src_on_device != 0;
@@ -1119,7 +1147,7 @@ namespace {
 mk_status field_spectrum_copy(mk_plan_t p, Survey& sv, void* packed, int r0, int rc, size_t bytes, int on_device,
                               bool out) {
   const mk::SurveyDev& v = sv.dev;
-  const int parts = v.rprec == MK_R_C64 ? 1 : (v.rprec == MK_R_SPLIT3_BF16 ? 3 : 2);
+  const int parts = mk::field_in_nw(v) ? 1 : (v.rprec == MK_R_SPLIT3_BF16 ? 3 : 2);
   const size_t need = (size_t)parts * v.nw * v.F * rc * 8;
   if (bytes < need) return fail(p, MK_ERR_ARG, "field spectrum rows need %zu bytes, %zu given", need, bytes);
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : (out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
@@ -1127,7 +1155,7 @@ mk_status field_spectrum_copy(mk_plan_t p, Survey& sv, void* packed, int r0, int
   for (int q = 0; q < parts; ++q) {
     size_t pitch, width, height;
     char* op;
-    if (v.rprec == MK_R_C64) {
+    if (mk::field_in_nw(v)) {
       pitch = (size_t)v.r_pad * sizeof(float2);
       width = (size_t)rc * sizeof(float2);
       height = (size_t)v.nw * v.F;

@@ -601,7 +601,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
     //    so the segments are 16-byte aligned); a ragged one element by element.
     if (ntr == bt) {
       const int kr = k0 + s.row0;  // on the field spectrum's r axis (row0 is a multiple of 32)
-      if (s.rprec == 0) {
+      if (field_in_nw(s)) {
         store_block_nw(s, st, ldm, bf, kr, bt, lbt);
       } else if (s.rprec == 2) {
         store_block_embedding<false, 2>(s, st, ldm, bf, kr, bt, lbt);
@@ -612,7 +612,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       }
     } else if (pc < ntr) {
       const int k = k0 + pc + s.row0;
-      if (s.rprec == 0) {
+      if (field_in_nw(s)) {
         float2* dst = s.Nw + (int64_t)pm0 * s.nw_stride + (int64_t)bf * s.r_pad + k;
         const int64_t dstep = (int64_t)pms * s.nw_stride;
         for (int m = pm0; m < nw; m += pms, dst += dstep) *dst = st[m * ldm + pc];

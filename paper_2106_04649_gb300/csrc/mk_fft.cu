@@ -346,7 +346,7 @@ __device__ __forceinline__ void stage_store(const SurveyDev& s, const float2* st
   const int t = tb + cc;
   const int f = t / s.ns, k = t - f * s.ns + s.row0;  // k on the field spectrum's r axis
   const float2* row = stage + cc * ld;
-  if (s.rprec == 0) {
+  if (field_in_nw(s)) {
     float2* dst = s.Nw + (int64_t)f * s.r_pad + k;
     for (int m = mc; m < s.nw; m += mstep) dst[(int64_t)m * s.nw_stride] = row[m];
   } else if (s.rprec >= 8) {

@@ -36,7 +36,9 @@ struct SurveyDev {
   void* Bq0;        // 16-bit field embedding [nw][2F][2 r_pad], hi part
   void* Bq1;        // lo (mid for the 3-way split) part
   void* Bq2;        // lo part of the 3-way split
-  float2* Nw;       // [nw][F][r_pad]
+  float2* Nw;       // [nw][F][r_pad] (complex FP32 R, and the FP32 field of the scaled FP16 split)
+  float* rsc;       // [nw] power-of-two scale of R_m (scaled FP16 split), else null
+  float* nsc;       // [nw][F] power-of-two scale of the field spectrum (scaled FP16 split), else null
   float2* S;        // [nw][s_stride]
   float* fN;        // [F][ns][nt] last N_i
   float* f1p;
@@ -65,6 +67,21 @@ struct SurveyDev {
                       // the epilogue when it reads S
 };
 
+// Storage precisions whose epilogue writes the complex FP32 field spectrum Nw
+// (complex FP32 R, and the scaled FP16 split, which quantises Nw at each
+// contraction); the other 16-bit forms write their embedding directly.
+__host__ __device__ inline bool field_in_nw(const SurveyDev& s) { return s.rprec == 0 || s.rprec == 5; }
+
+// Power-of-two scale that maps a largest magnitude amax into [2^14, 2^15):
+// with it the FP16 hi part of every value and the lo part of values down to
+// 2^-17 of amax stay normal.  1 for amax = 0 (or not finite).
+__host__ __device__ inline float f16_scale(float amax) {
+  if (!(amax > 0.f) || !(amax < 3.0e38f)) return 1.f;
+  int e;
+  frexpf(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+  return ldexpf(1.f, 15 - e < 126 ? 15 - e : 126);  // finite for the smallest magnitudes
+}
+
 // Kernel launchers (return the launch status; the caller checks it).
 struct UmmaMaps;  // tensor maps of the tcgen05 contraction (mk_umma.cu)
 UmmaMaps* umma_create(const SurveyDev& s);
@@ -76,6 +93,13 @@ cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t
 cudaError_t prepare_load();
 cudaError_t launch_load_rows_q(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
                                int max_blocks);
+// scaled FP16 split: the largest |Re|, |Im| per frequency of rows row0 .. row0 + rows
+// (whole frequencies) into s.rsc as the bits of a float (atomic max; cleared first)
+cudaError_t launch_r_amax(const float2* src, const SurveyDev& s, int64_t row0, int64_t rows, cudaStream_t st,
+                          int max_blocks);
+cudaError_t launch_r_scale(const SurveyDev& s, int w_begin, int w_count, cudaStream_t st);  // amax -> scale
+// scaled FP16 split: per (frequency, focal point) the scale of Nw and its 2-part embedding
+cudaError_t launch_quantize_field(const SurveyDev& s, cudaStream_t st, int num_sms);
 // Energies of iteration i go to ring[(i % slots) * F + f].
 cudaError_t launch_epilogue(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms);
 cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st);

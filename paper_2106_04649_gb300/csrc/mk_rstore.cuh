@@ -1,7 +1,8 @@
 // Conversion of one complex FP32 value of R into the 16-bit storage of the
 // tensor-core contraction: BF16 or FP16 rounded to nearest even (q = 1, 2),
 // BF16 hi + lo with lo = rn(x - hi) (q = 3), or BF16 hi + mid + lo with
-// mid = rn(x - hi), lo = rn(x - hi - mid) (q = 4).  idx counts complex
+// mid = rn(x - hi), lo = rn(x - hi - mid) (q = 4), or FP16 hi + lo of the
+// value scaled by its frequency's power of two s.rsc[m] (q = 5).  idx counts complex
 // elements of the [nw][ns][r_pad] layout; each part holds one 16-bit pair
 // per element.  Shared by the R loads from band spectra and from time traces.
 #pragma once
@@ -14,6 +15,15 @@
 namespace mk {
 
 __device__ __forceinline__ void store_r16(const SurveyDev& s, int q, int64_t idx, float2 v) {
+  if (q == 5) {  // FP16 hi + lo of the value scaled by the power of two of its frequency
+    const float sc = s.rsc[idx / ((int64_t)s.ns * s.r_pad)];
+    const float x = v.x * sc, y = v.y * sc;  // exact: a power of two
+    const __half2 h = __floats2half2_rn(x, y);
+    const float2 hf = __half22float2(h);
+    reinterpret_cast<__half2*>(const_cast<void*>(s.Rq0))[idx] = h;
+    reinterpret_cast<__half2*>(const_cast<void*>(s.Rq1))[idx] = __floats2half2_rn(x - hf.x, y - hf.y);
+    return;
+  }
   if (q == 2) {
     reinterpret_cast<__half2*>(const_cast<void*>(s.Rq0))[idx] = __floats2half2_rn(v.x, v.y);
     return;

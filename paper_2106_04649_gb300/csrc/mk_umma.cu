@@ -15,7 +15,10 @@
 //    (about 16 significant bits per operand);
 //  * 3-way split BF16 (hi + mid + lo for R and the field):
 //    D = hh + hm + mh + hl + lh + mm, the six products down to 2^-16 of the
-//    leading term (about 24 significant bits, FP32-like).
+//    leading term (about 24 significant bits, FP32-like);
+//  * scaled FP16 split (hi + lo, each operand scaled by a power of two into
+//    FP16's normal range, mk_quant.cu): D = hh + hl + lh, about 22 significant
+//    bits per operand; the epilogue divides the scales out.
 //
 // Kernel: persistent, one CTA per SM, warp-specialised:
 //  warp 0 lane 0 : TMA producer (3-D tensor maps [K', rows, frequency],
@@ -73,6 +76,8 @@ struct UmmaParams {
   float c;
   int* err;
   unsigned* queue;  // [2]: next tile, finished CTAs (the last CTA resets both)
+  const float* rsc;  // scaled FP16 split: [nw] scale of R_m, else null
+  const float* nsc;  // [nw][F] scale of the field spectrum (with rsc)
 };
 
 constexpr int kTQ = 4;  // tile-index slots between the producer and the MMA and epilogue warps
@@ -368,9 +373,21 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
         }
         if (row < P.ns) {
           const int f0 = nt * BN / 2;
+          if (P.rsc) {  // the operands were scaled by powers of two: divide them out
+            const float cm = P.c / P.rsc[m];
+            const float* ns_m = P.nsc + (int64_t)m * P.F;
 #pragma unroll
-          for (int j = 0; j < BN / 2; ++j)
-            if (f0 + j < P.F) scol[(int64_t)(f0 + j) * P.ns] = make_float2(P.c * accv[2 * j], P.c * accv[2 * j + 1]);
+            for (int j = 0; j < BN / 2; ++j)
+              if (f0 + j < P.F) {
+                const float q = cm / ns_m[f0 + j];
+                scol[(int64_t)(f0 + j) * P.ns] = make_float2(q * accv[2 * j], q * accv[2 * j + 1]);
+              }
+          } else {
+#pragma unroll
+            for (int j = 0; j < BN / 2; ++j)
+              if (f0 + j < P.F)
+                scol[(int64_t)(f0 + j) * P.ns] = make_float2(P.c * accv[2 * j], P.c * accv[2 * j + 1]);
+          }
         }
         continue;
       }
@@ -436,6 +453,8 @@ cudaError_t launch_bn(const SurveyDev& s, const UmmaMaps& mp, cudaStream_t st, i
   P.c = s.c;
   P.err = s.err;
   P.queue = s.counter + 4;
+  P.rsc = s.rsc;
+  P.nsc = s.nsc;
   const int64_t tiles = (int64_t)P.nw * P.mtiles * P.ntiles;
   const int grid = (int)(tiles < num_sms ? tiles : num_sms);
   umma_cgemm_kernel<BN, NA, NB, FMT, PROMOTE><<<grid, kThreads, smem, st>>>(mp.a0, mp.a1, mp.a2, mp.b0, mp.b1, mp.b2, P,
@@ -506,6 +525,7 @@ cudaError_t umma_prepare() {
   cudaError_t e;
   if ((e = set_attr_na<3, 3, 1, true>()) != cudaSuccess) return e;
   if ((e = set_attr_na<2, 2, 1, true>()) != cudaSuccess) return e;
+  if ((e = set_attr_na<2, 2, 0, true>()) != cudaSuccess) return e;
   if ((e = set_attr_na<1, 2, 1, false>()) != cudaSuccess) return e;
   return set_attr_na<1, 2, 0, false>();
 }
@@ -521,9 +541,9 @@ int umma_bn(int F) {
 UmmaMaps* umma_create(const SurveyDev& s) {
   UmmaMaps* mp = new UmmaMaps();
   mp->bn = umma_bn(s.F);
-  mp->na = s.rprec == 3 ? 2 : (s.rprec == 4 ? 3 : 1);
+  mp->na = (s.rprec == 3 || s.rprec == 5) ? 2 : (s.rprec == 4 ? 3 : 1);
   mp->nb = s.rprec == 4 ? 3 : 2;
-  mp->fmt = s.rprec == 2 ? 0 : 1;
+  mp->fmt = (s.rprec == 2 || s.rprec == 5) ? 0 : 1;
   const int kp = 2 * s.r_pad;
   bool ok = encode_map(&mp->a0, s.Rq0, kp, s.ns, s.nw, UM, mp->fmt) &&
             encode_map(&mp->a1, mp->na >= 2 ? s.Rq1 : s.Rq0, kp, s.ns, s.nw, UM, mp->fmt) &&
@@ -558,6 +578,7 @@ cudaError_t launch_umma(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t st,
   if (!mp) return cudaErrorInvalidValue;
   // the split forms target FP32-level accuracy: they promote per K block
   if (mp->na == 3) return launch_na<3, 3, 1, true>(s, *mp, st, num_sms);
+  if (mp->na == 2 && mp->fmt == 0) return launch_na<2, 2, 0, true>(s, *mp, st, num_sms);  // scaled FP16 split
   if (mp->na == 2) return launch_na<2, 2, 1, true>(s, *mp, st, num_sms);
   if (mp->fmt == 1) return launch_na<1, 2, 1, false>(s, *mp, st, num_sms);
   return launch_na<1, 2, 0, false>(s, *mp, st, num_sms);

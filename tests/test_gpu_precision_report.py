@@ -4,9 +4,10 @@ The precision workload: the paper-small survey with 601 focal points along
 z = 1200 m; the GPU runs all 601 and the oracle follows four of them (the
 same complex64 R, FP64).  After each of
 the 16 iterations the fields of those four are compared.  The table is
-printed (pytest -s shows it); the gates are the contract's: complex FP32 and
-the 3-way split BF16 within 1e-5 for f1+, f1- and G at every iteration and
-1e-4 for N; the 16-bit forms (R stored with 8 or 11 significant bits) are
+printed (pytest -s shows it); the gates are the contract's: complex FP32, the
+3-way split BF16 (6 products) and the scaled FP16 split (3 products) within
+1e-5 for f1+, f1- and G at every iteration and 1e-4 for N; the 16-bit forms
+(R stored with 8 or 11 significant bits) and the 3-product BF16 split are
 reported, with only a loose sanity bound.
 """
 
@@ -20,7 +21,7 @@ from tests.helpers import desc_for
 
 pytestmark = pytest.mark.gpu
 
-FORMS = [("c64", 0), ("cbf16", 1), ("cf16", 2), ("split", 3), ("split3", 4)]
+FORMS = [("c64", 0), ("cbf16", 1), ("cf16", 2), ("split", 3), ("split3", 4), ("splitf16", 5)]
 SEL = [0, 200, 400, 600]
 NITER = 16
 
@@ -57,7 +58,7 @@ def test_per_iteration_error_table():
     print("iter " + " ".join(f"{n + ' N':>12s} {n + ' G':>12s}" for n, _ in FORMS))
     for i in range(NITER):
         print(f"{i:4d} " + " ".join(f"{table[n][i, 0]:12.3e} {table[n][i, 3]:12.3e}" for n, _ in FORMS))
-    for name in ("c64", "split3"):
+    for name in ("c64", "split3", "splitf16"):
         t = table[name]
         assert np.all(t[:, 1:] <= 1e-5), (name, t[:, 1:].max())
         assert np.all(t[:, 0] <= 1e-4), (name, t[:, 0].max())

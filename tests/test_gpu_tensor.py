@@ -15,7 +15,7 @@ from tests.helpers import FIELD_NAMES, desc_for, survey_inputs
 
 pytestmark = pytest.mark.gpu
 
-C64, CBF16, CF16, SPLIT, SPLIT3 = 0, 1, 2, 3, 4
+C64, CBF16, CF16, SPLIT, SPLIT3, SPLITF16 = 0, 1, 2, 3, 4, 5
 
 
 def bf16_rne(x):
@@ -128,7 +128,8 @@ def test_paper_small_F64_split_bf16_sampled():
         assert err <= (1e-4 if name == "N" else 3e-5), f"{name}: {err:.3e}"
 
 
-@pytest.mark.parametrize("rprec,exact", [(CBF16, False), (SPLIT, False), (SPLIT3, False), (SPLIT3, True)])
+@pytest.mark.parametrize("rprec,exact", [(CBF16, False), (SPLIT, False), (SPLIT3, False), (SPLIT3, True),
+                                         (SPLITF16, True)])
 def test_paper_small_per_iteration_identical_inputs(rprec, exact):
     # one tensor-core synthesis + epilogue from the oracle's state, vs the oracle on
     # the dequantised R (exact=False) or on the exact complex64 R (split form, exact=True)
@@ -167,3 +168,65 @@ def test_paper_small_F64_split3_bf16_vs_exact():
     for j, name in enumerate(FIELD_NAMES):
         err = rel_l2(f[j][sel], ref[j])
         assert err <= (1e-4 if name == "N" else 1e-5), f"{name}: {err:.3e}"
+
+
+@pytest.mark.parametrize("n,nt,nfocal,fmax", [(25, 128, 3, None), (40, 128, 8, 40.0), (7, 64, 1, None),
+                                              (75, 256, 5, 60.0)])
+def test_scaled_fp16_split_vs_exact_oracle_per_iteration(n, nt, nfocal, fmax):
+    # the 3-product form with both operands split into FP16 hi + lo and scaled by
+    # powers of two (R per frequency, the field per frequency and focal point):
+    # <= 1e-5 against the exact FP64 oracle at every iteration, like the 6-product form
+    s = small_survey(n=n, nt=nt, nfocal=min(nfocal, 3), fmax_hz=fmax)
+    if nfocal > 3:
+        xs = np.linspace(0.2, 0.8, nfocal) * (n - 1) * s.dx
+        s.focal = np.stack([xs, np.full(nfocal, 650.0)], axis=1)
+    R, td, Gd = survey_inputs(s)
+    _, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 6, history=True)
+    got = _run(s, R, Gd, td, SPLITF16, 6, per_iter=True)
+    for i, (e, f) in enumerate(got):
+        ref = _ref(hist[i])
+        for j, name in enumerate(FIELD_NAMES):
+            err = rel_l2(f[j], ref[j])
+            assert err <= (1e-4 if name == "N" else 1e-5), f"n={n} F={nfocal} iter {i} {name}: {err:.3e}"
+
+
+def test_paper_small_F64_scaled_fp16_split_vs_exact():
+    # the 3-product scaled FP16 split on the paper-small survey: <= 1e-5 relative L2
+    # against the exact FP64 oracle after 16 iterations (sampled focal points)
+    s = S.paper_small_survey(64)
+    R, td, Gd = survey_inputs(s)
+    (e, f), = _run(s, R, Gd, td, SPLITF16, 16)
+    sel = [0, 31, 63]
+    st = M.run(R.astype(np.complex128), Gd[sel].astype(np.float64), td[sel], s.eps, s.dt, s.dx, 16)
+    ref = _ref(st)
+    for j, name in enumerate(FIELD_NAMES):
+        err = rel_l2(f[j][sel], ref[j])
+        assert err <= (1e-4 if name == "N" else 1e-5), f"{name}: {err:.3e}"
+    eref = np.array(st.energy)
+    assert np.max(np.abs(e[:, sel] - eref) / eref) <= 1e-4
+
+
+def test_scaled_fp16_split_load_paths_agree():
+    # host (pageable, staged), pinned and device sources give the same scales and parts
+    import torch
+    from paper_2106_04649_gb300.api import Plan
+    s = small_survey(n=40, nt=128, nfocal=3, fmax_hz=40.0)
+    R, td, Gd = survey_inputs(s)
+    outs = []
+    for mode in ("pageable", "pinned", "device"):
+        p = Plan([desc_for(s, rprec=SPLITF16)])
+        if mode == "pageable":
+            p.load_R(0, R[:10])
+            p.load_R(0, R[10:], w_begin=10)
+        elif mode == "pinned":
+            Rp = torch.from_numpy(R).pin_memory()
+            from paper_2106_04649_gb300 import binding as B
+            B.mk_load_R(p.handle, 0, Rp.data_ptr(), 0, R.shape[0], 0)
+        else:
+            p.load_R(0, torch.from_numpy(R).cuda())
+        p.set_Gd_window(0, Gd, td, s.eps)
+        e = p.iterate(3)
+        outs.append((e, p.fetch_fields(0)))
+        p.close()
+    for e, f in outs[1:]:
+        assert np.array_equal(e, outs[0][0]) and np.array_equal(f, outs[0][1])
