@@ -49,36 +49,64 @@ __global__ void r_scale_kernel(float* rsc, int w_begin, int w_count) {
   if (i < w_count) rsc[w_begin + i] = f16_scale(__uint_as_float(reinterpret_cast<unsigned*>(rsc)[w_begin + i]));
 }
 
-// one warp per (m, f) row of Nw (r_pad values, the padding zero)
+// The 2-part FP16 embedding of two consecutive values (a, b) of one row,
+// scaled by sc, as 8-byte stores into rows 2f and 2f+1 of both parts.
+__device__ __forceinline__ void put_pair(uint32_t* b0, uint32_t* b1, int64_t w, int64_t rp, float4 ab, float sc) {
+  float hr0, hi0, hr1, hi1, lr, li;
+  const uint32_t h0 = round_pair<false>(ab.x * sc, ab.y * sc, hr0, hi0);
+  const uint32_t h1 = round_pair<false>(ab.z * sc, ab.w * sc, hr1, hi1);
+  const uint32_t l0 = round_pair<false>(ab.x * sc - hr0, ab.y * sc - hi0, lr, li);
+  const uint32_t l1 = round_pair<false>(ab.z * sc - hr1, ab.w * sc - hi1, lr, li);
+  *reinterpret_cast<uint2*>(b0 + w) = make_uint2(pair_neg_hi(h0), pair_neg_hi(h1));
+  *reinterpret_cast<uint2*>(b0 + w + rp) = make_uint2(pair_swap(h0), pair_swap(h1));
+  *reinterpret_cast<uint2*>(b1 + w) = make_uint2(pair_neg_hi(l0), pair_neg_hi(l1));
+  *reinterpret_cast<uint2*>(b1 + w + rp) = make_uint2(pair_swap(l0), pair_swap(l1));
+}
+
+// One warp per (m, f) row of Nw (r_pad values, a multiple of 32, the padding
+// zero), two values per lane and step.  PER > 0: the row is held in
+// registers (r_pad <= 64 PER), one read; PER = 0: two reads.
+template <int PER>
 __global__ void __launch_bounds__(256) quantize_kernel(SurveyDev s) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t nrows = (int64_t)s.nw * s.F;
+  const int npair = s.r_pad / 2;
   uint32_t* b0 = reinterpret_cast<uint32_t*>(s.Bq0);
   uint32_t* b1 = reinterpret_cast<uint32_t*>(s.Bq1);
   for (int64_t row = warp; row < nrows; row += nwarps) {
     const int m = (int)(row / s.F), f = (int)(row - (int64_t)m * s.F);
-    const float2* src = s.Nw + (int64_t)m * s.nw_stride + (int64_t)f * s.r_pad;
-    float mx = 0.f;
-    for (int i = lane; i < s.r_pad; i += 32) {
-      const float2 v = src[i];
-      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const float sc = f16_scale(mx);
-    if (lane == 0) s.nsc[row] = sc;
+    const float4* src = reinterpret_cast<const float4*>(s.Nw + (int64_t)m * s.nw_stride + (int64_t)f * s.r_pad);
     const int64_t w0 = ((int64_t)m * 2 * s.F + 2 * f) * s.r_pad;  // 32-bit word of row 2f, position 0
-    for (int i = lane; i < s.r_pad; i += 32) {
-      const float2 v = src[i];
-      float hr, hi, lr, li;
-      const uint32_t h = round_pair<false>(v.x * sc, v.y * sc, hr, hi);
-      const uint32_t l = round_pair<false>(v.x * sc - hr, v.y * sc - hi, lr, li);
-      b0[w0 + i] = pair_neg_hi(h);
-      b0[w0 + s.r_pad + i] = pair_swap(h);
-      b1[w0 + i] = pair_neg_hi(l);
-      b1[w0 + s.r_pad + i] = pair_swap(l);
+    float mx = 0.f;
+    if constexpr (PER > 0) {
+      float4 v[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int i = lane + 32 * u;
+        v[u] = i < npair ? src[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float sc = f16_scale(mx);
+      if (lane == 0) s.nsc[row] = sc;
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int i = lane + 32 * u;
+        if (i < npair) put_pair(b0, b1, w0 + 2 * i, s.r_pad, v[u], sc);
+      }
+    } else {
+      for (int i = lane; i < npair; i += 32) {
+        const float4 v = src[i];
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float sc = f16_scale(mx);
+      if (lane == 0) s.nsc[row] = sc;
+      for (int i = lane; i < npair; i += 32) put_pair(b0, b1, w0 + 2 * i, s.r_pad, src[i], sc);
     }
   }
 }
@@ -103,7 +131,16 @@ cudaError_t launch_quantize_field(const SurveyDev& s, cudaStream_t st, int num_s
   const int64_t rows = (int64_t)s.nw * s.F;
   int64_t grid = (rows + 7) / 8;
   if (grid > (int64_t)num_sms * 8) grid = (int64_t)num_sms * 8;
-  quantize_kernel<<<(unsigned)grid, 256, 0, st>>>(s);
+  const int per = (s.r_pad + 63) / 64;  // float4 pairs per lane
+  if (per <= 4) {
+    quantize_kernel<4><<<(unsigned)grid, 256, 0, st>>>(s);
+  } else if (per <= 10) {
+    quantize_kernel<10><<<(unsigned)grid, 256, 0, st>>>(s);
+  } else if (per <= 20) {
+    quantize_kernel<20><<<(unsigned)grid, 256, 0, st>>>(s);
+  } else {
+    quantize_kernel<0><<<(unsigned)grid, 256, 0, st>>>(s);
+  }
   return cudaGetLastError();
 }
 

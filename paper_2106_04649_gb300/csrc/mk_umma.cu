@@ -180,6 +180,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
   __shared__ __align__(8) uint64_t tq_empty[kTQ];  // read by the MMA lane and the 4 epilogue warps
   __shared__ int tq[kTQ];                           // tile index, -1 ends the work
   __shared__ uint32_t tmem_slot;
+  __shared__ float sfac[4][64];                     // per epilogue warp: output factors of the tile's columns
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t ring = (smem_u32(smem_raw) + 1023u) & ~1023u;
@@ -350,6 +351,15 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
         float accv[BN];
 #pragma unroll
         for (int i = 0; i < BN; ++i) accv[i] = 0.f;
+        // scaled operands: the scales of this tile's columns are loaded now and
+        // used after the K loop (their latency hides behind it)
+        const int f0 = nt * BN / 2;
+        float rs = 1.f, n0 = 1.f, n1 = 1.f;
+        if (P.rsc) {
+          rs = __ldg(P.rsc + m);
+          if (lane < BN / 2 && f0 + lane < P.F) n0 = __ldg(P.nsc + (int64_t)m * P.F + f0 + lane);
+          if (lane + 32 < BN / 2 && f0 + lane + 32 < P.F) n1 = __ldg(P.nsc + (int64_t)m * P.F + f0 + lane + 32);
+        }
         bool ok = true;
         for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
           const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
@@ -371,15 +381,17 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
           if (lane == 0 && P.err) atomicExch(P.err, 13);
           break;
         }
+        if (P.rsc) {  // the operands were scaled by powers of two: c / (scale of R_m x scale of column)
+          sfac[quad][lane] = P.c / (rs * n0);
+          sfac[quad][lane + 32] = P.c / (rs * n1);
+          __syncwarp();
+        }
         if (row < P.ns) {
-          const int f0 = nt * BN / 2;
-          if (P.rsc) {  // the operands were scaled by powers of two: divide them out
-            const float cm = P.c / P.rsc[m];
-            const float* ns_m = P.nsc + (int64_t)m * P.F;
+          if (P.rsc) {
 #pragma unroll
             for (int j = 0; j < BN / 2; ++j)
               if (f0 + j < P.F) {
-                const float q = cm / ns_m[f0 + j];
+                const float q = sfac[quad][j];
                 scol[(int64_t)(f0 + j) * P.ns] = make_float2(q * accv[2 * j], q * accv[2 * j + 1]);
               }
           } else {
@@ -389,6 +401,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
                 scol[(int64_t)(f0 + j) * P.ns] = make_float2(P.c * accv[2 * j], P.c * accv[2 * j + 1]);
           }
         }
+        __syncwarp();  // sfac is rewritten by the next tile
         continue;
       }
       const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
