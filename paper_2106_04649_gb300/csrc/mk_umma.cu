@@ -39,7 +39,8 @@
 // Accuracy: the tensor core's FP32 accumulation over a long K chain carries
 // a rounding bias that, on cancelling sums, dominates the operand precision
 // of the split forms.  With PROMOTE the MMAs of each 64-wide K block start a
-// fresh accumulator (two TMEM buffers alternate) and the epilogue warps add
+// fresh accumulator (four TMEM buffers rotate, two for N tiles above 128
+// columns) and the epilogue warps add
 // each block's partial sums into FP32 registers with round-to-nearest adds.
 // Every mbarrier wait is bounded; on time-out the CTA records an error word,
 // drains its copies and MMAs, frees TMEM and returns.
@@ -168,13 +169,17 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
   constexpr int A_BYTES = UM * UKB * 2;
   constexpr int B_BYTES = BN * UKB * 2;
   constexpr int STAGE_BYTES = NA * A_BYTES + NB * B_BYTES;
-  constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
+  // TMEM accumulators: two (one per tile, alternating) without promotion; with
+  // promotion one per K block, four of them where TMEM's 512 columns allow, so
+  // that the MMAs run up to three K blocks ahead of the epilogue's drain
+  constexpr int NACC = PROMOTE && 4 * BN <= 512 ? 4 : 2;
+  constexpr int TMEM_COLS = NACC * BN < 32 ? 32 : NACC * BN;
   constexpr uint32_t IDESC = make_idesc(FMT, BN);
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
-  __shared__ __align__(8) uint64_t tfull[2];
-  __shared__ __align__(8) uint64_t tempty[2];
+  __shared__ __align__(8) uint64_t tfull[4];
+  __shared__ __align__(8) uint64_t tempty[4];
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ __align__(8) uint64_t tq_full[kTQ];   // tile index written
   __shared__ __align__(8) uint64_t tq_empty[kTQ];  // read by the MMA lane and the 4 epilogue warps
@@ -192,7 +197,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < NACC; ++a) {
       mbar_init(smem_u32(&tfull[a]), 1);
       mbar_init(smem_u32(&tempty[a]), 4);
     }
@@ -280,8 +285,8 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
         }
         for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
           if (PROMOTE) {  // one fresh accumulator per K block, buffers alternate
-            acc = it & 1u;
-            aph = (it >> 1) & 1u;
+            acc = it % NACC;
+            aph = (it / NACC) & 1u;
             if (!mbar_wait(smem_u32(&tempty[acc]), aph ^ 1u)) {
               ok = false;
               break;
@@ -362,7 +367,7 @@ umma_cgemm_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constan
         }
         bool ok = true;
         for (int kb = 0; kb < P.kblocks; ++kb, ++it) {
-          const uint32_t buf = it & 1u, ph = (it >> 1) & 1u;
+          const uint32_t buf = it % NACC, ph = (it / NACC) & 1u;
           ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&tfull[buf]), ph));
           if (!ok) break;
           tc_fence_after();
