@@ -253,6 +253,10 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
+// bytes [a, a + n) into L2 (a and n multiples of 16)
+__device__ __forceinline__ void prefetch_l2(const void* a, unsigned n) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -398,20 +402,10 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
     const int tb = bf * s.ns + k0;
     const int ntr = s.ns - k0 < bt ? s.ns - k0 : bt;
     float2* st = stage_base + buf * stage_elems;
-    if (pc < ntr && !s.pacc) {
+    if (pc < ntr) {
       const float2* src = s.S + (int64_t)pm0 * s.s_stride + tb + pc;
       const int64_t sstep = (int64_t)pms * s.s_stride;
       for (int m = pm0; m < nw; m += pms, src += sstep) cp_async8(st + m * ldm + pc, src);
-    } else if (pc < ntr) {
-      // the same through registers, and pmin's band spectrum += S (one thread
-      // owns each (m, t))
-      for (int m = pm0; m < nw; m += pms) {
-        const int64_t i = (int64_t)m * s.s_stride + tb + pc;
-        const float2 v = __ldg(s.S + i);
-        const float2 a = s.pacc[i];
-        st[m * ldm + pc] = v;
-        s.pacc[i] = make_float2(a.x + v.x, a.y + v.y);
-      }
     }
     int* sL = sL_base + buf * bt;
     for (int c = threadIdx.x; c < bt; c += kThreads) sL[c] = c < ntr ? s.L[tb + c] : 0;
@@ -440,6 +434,17 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
     const int k0 = (blk - bf * nkb) * bt;
     const int tb = bf * s.ns + k0;
     const int ntr = s.ns - k0 < bt ? s.ns - k0 : bt;
+    if (s.pacc) {
+      // pmin's band spectrum += S from the stage, as fire-and-forget
+      // reductions (one per (m, t) and launch: the same sum in any schedule),
+      // before the transforms overwrite the stage
+      if (pc < ntr) {
+        float2* acc = s.pacc + (int64_t)pm0 * s.s_stride + tb + pc;
+        const int64_t astep = (int64_t)pms * s.s_stride;
+        for (int m = pm0; m < nw; m += pms, acc += astep) atomicAdd(acc, st[m * ldm + pc]);
+      }
+      __syncthreads();
+    }
 
     for (int r = 0; r < rounds; ++r) {
       const int c = r * (kWarps * TPW) + warp * TPW + grp;  // stage column of this group's trace
@@ -447,6 +452,15 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       const int L = active ? sL[c] : 0;
       float* __restrict__ ft = f1 + (int64_t)(tb + (active ? c : 0)) * NT;  // this trace of f1
       float2* col = st + c;
+      if (active && p == 0 && L > 0) {
+        // the window samples j < L and j > nt - L of f1 (both parities touch
+        // only these) into L2 while the inverse transform runs: 16-byte
+        // aligned ranges (the trace starts on a 16-byte boundary)
+        const unsigned n0 = (unsigned)((4 * L + 15) & ~15);
+        const int j2 = L > NT ? 0 : (NT - L + 1) & ~3;  // L <= nt/2 + 1 from the window kernel
+        prefetch_l2(ft, n0 < 4u * NT ? n0 : 4u * NT);
+        if (j2 < NT) prefetch_l2(ft + j2, 4u * (unsigned)(NT - j2));
+      }
       // Bounds in register index e, once per trace (inactive groups: none):
       //  band bins k = p + P e < nw  <=>  e < ek;  M - k < nw  <=>  e >= em;
       //  window samples j0 = 2(p + P e): j0 < L <=> e < a0, j0 > nt - L <=> e >= b0;

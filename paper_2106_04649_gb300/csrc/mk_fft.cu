@@ -403,43 +403,29 @@ epilogue_kernel(SurveyDev s, double* __restrict__ ring, int slots, int G) {
     const int ntr = s.ncols - tb < bt ? s.ncols - tb : bt;
     // 1. the block's band spectra, one coalesced pass (bt is a power of two
     //    dividing THREADS, so each thread keeps one trace column c)
-    if (cc < ntr && !s.pacc) {
+    if (cc < ntr) {
+      // eight predicated loads in flight per thread, then the stage stores;
+      // with a pmin band spectrum kept, pmin += S as fire-and-forget
+      // reductions (one per (m, t) and launch, so the sum is the same in
+      // any schedule)
       const float2* src = s.S + tb + cc;
       float2* dst = stage + cc * ld;
-      int m = mc;
-      for (; m + 7 * mstep < s.nw; m += 8 * mstep) {  // eight loads in flight per thread
+      float2* acc = s.pacc ? s.pacc + tb + cc : nullptr;
+      for (int m0 = mc; m0 < s.nw; m0 += 8 * mstep) {
         float2 v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = __ldg(src + (int64_t)(m + u * mstep) * s.s_stride);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) dst[m + u * mstep] = v[u];
-      }
-      for (; m < s.nw; m += mstep) dst[m] = __ldg(src + (int64_t)m * s.s_stride);
-    } else if (cc < ntr) {
-      // the same, and pmin's band spectrum += S (one thread owns each (m, t)),
-      // eight pairs of loads in flight per thread
-      float2* dst = stage + cc * ld;
-      const float2* src = s.S + tb + cc;
-      float2* acc = s.pacc + tb + cc;
-      int m = mc;
-      for (; m + 7 * mstep < s.nw; m += 8 * mstep) {
-        float2 v[8], a[8];
-#pragma unroll
         for (int u = 0; u < 8; ++u) {
-          v[u] = __ldg(src + (int64_t)(m + u * mstep) * s.s_stride);
-          a[u] = acc[(int64_t)(m + u * mstep) * s.s_stride];
+          const int m = m0 + u * mstep;
+          if (m < s.nw) v[u] = __ldg(src + (int64_t)m * s.s_stride);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          dst[m + u * mstep] = v[u];
-          acc[(int64_t)(m + u * mstep) * s.s_stride] = make_float2(a[u].x + v[u].x, a[u].y + v[u].y);
+          const int m = m0 + u * mstep;
+          if (m < s.nw) {
+            dst[m] = v[u];
+            if (acc) atomicAdd(acc + (int64_t)m * s.s_stride, v[u]);
+          }
         }
-      }
-      for (; m < s.nw; m += mstep) {
-        const float2 v = __ldg(src + (int64_t)m * s.s_stride);
-        const float2 a = acc[(int64_t)m * s.s_stride];
-        dst[m] = v;
-        acc[(int64_t)m * s.s_stride] = make_float2(a.x + v.x, a.y + v.y);
       }
     }
     if (threadIdx.x < ntr) sL[threadIdx.x] = s.L[tb + threadIdx.x];  // the block's window lengths
