@@ -15,7 +15,7 @@ Metric: focal points per second to convergence (16 iterations), with the
 contraction's HBM bandwidth and FLOP rate against the measured roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--nfocal 1|64|601]
-                    [--rprec c64|cbf16|cf16|split|split3] [--impl ours|reference]
+                    [--rprec c64|cbf16|cf16|split|split3|splitf16] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle on the host cores (the slow
 baseline) on the same workload, on a bounded sample of focal points.
@@ -637,7 +637,7 @@ def main_ours(args):
         # large survey: 4001 x 4001, nt = 4096, 984 bins; the 4001-point line in focal batches,
         # the largest batch (128, else 64) whose plan fits in device memory
         import gc
-        for lp in ("split3", "c64"):
+        for lp in ("split3", "splitf16", "cf16", "c64"):
             for fb in (128, 64):
                 ls = S.large_survey(nfocal=fb)
                 try:

@@ -22,7 +22,7 @@ cudaError_t launch_contract(const SurveyDev& s, const UmmaMaps* mp, cudaStream_t
     return e != cudaSuccess ? e : launch_umma(s, mp, st, num_sms);
   }
   if (s.rprec != 0) return launch_umma(s, mp, st, num_sms);
-  if (s.F == 1) return launch_gemv(s, st, num_sms);
+  if (gemv_takes(s)) return launch_gemv(s, st, num_sms);
   return launch_cgemm_simt(s, st);
 }
 

@@ -194,25 +194,32 @@ __host__ __device__ constexpr int group_buf() { return P == 1 ? 0 : 32 * (P + 1)
 
 // Per-lane twiddle W_M^{p k2} (W_M = e^{-2 pi i / M}, M = nt/2) as the product
 // of two entries of the table e^{-2 pi i j / nt}: k2 = 8a + b,
-// W_M^{p k2} = W_M^{8 p a} W_M^{p b} (W_M^x = entry 2x mod nt).
+// W_M^{p k2} = W_M^{8 p a} W_M^{p b} (W_M^x = entry 2x mod nt).  The ten
+// factors of lane p (b = 1 .. 7, a = 1 .. 3) depend on p only: the CTA keeps
+// them in shared memory, factor j of lane p at tws[j P + p].
+constexpr int kLaneTw = 10;
 template <int NT>
-__device__ __forceinline__ void lane_twiddles(const float2* __restrict__ twl, int p, float2 (&wa)[4],
-                                              float2 (&wb)[8]) {
+__device__ __forceinline__ float2 lane_twiddle_entry(const float2* __restrict__ twl, int j, int p) {
+  return __ldg(twl + ((j < 7 ? 2 * p * (j + 1) : 16 * p * (j - 6)) & (NT - 1)));
+}
+template <int NT>
+__device__ __forceinline__ void lane_twiddles(const float2* tws, int p, float2 (&wa)[4], float2 (&wb)[8]) {
+  constexpr int P = NT / 64;
 #pragma unroll
-  for (int b = 1; b < 8; ++b) wb[b] = __ldg(twl + ((2 * p * b) & (NT - 1)));
+  for (int b = 1; b < 8; ++b) wb[b] = tws[(b - 1) * P + p];
 #pragma unroll
-  for (int a = 1; a < 4; ++a) wa[a] = __ldg(twl + ((16 * p * a) & (NT - 1)));
+  for (int a = 1; a < 4; ++a) wa[a] = tws[(6 + a) * P + p];
 }
 
 // Complex DFT of M = 32 P points over the P lanes of a group (lane p holds
 // n = p + P e at v[e]); afterwards lane q holds index k = q + P out_e(a) at
 // v[a].  gbuf is the group's shared buffer (half the transpose per pass).
 template <int NT, bool INV>
-__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, const float2* __restrict__ twl) {
+__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, const float2* tws) {
   constexpr int P = NT / 64;
   if constexpr (P > 1) {
     float2 wa[4], wb[8];
-    lane_twiddles<NT>(twl, p, wa, wb);
+    lane_twiddles<NT>(tws, p, wa, wb);
     dft<32, INV>(v);  // over e: v[k2]
     static_for<32>([&](auto K) {
       constexpr int k2 = decltype(K)::value;
@@ -253,10 +260,6 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
 }
-// bytes [a, a + n) into L2 (a and n multiples of 16)
-__device__ __forceinline__ void prefetch_l2(const void* a, unsigned n) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"(n) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -291,7 +294,8 @@ size_t epi_smem(int nw, int rounds, int nbuf) {
   constexpr int P = NT / 64;
   const int bt = kWarps * traces_per_warp<NT>() * rounds;
   return (size_t)nbuf * nw * (bt + 1) * sizeof(float2) +
-         (size_t)kWarps * traces_per_warp<NT>() * group_buf<P>() * sizeof(float2) + (size_t)nbuf * bt * sizeof(int);
+         (size_t)kWarps * traces_per_warp<NT>() * group_buf<P>() * sizeof(float2) +
+         (size_t)kLaneTw * P * sizeof(float2) + (size_t)nbuf * bt * sizeof(int);
 }
 
 // A full block's band spectra to Nw[m][f][k0 .. k0 + bt): 16-byte stores of
@@ -367,7 +371,9 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
   float2* stage_base = reinterpret_cast<float2*>(smem_raw);
   const size_t stage_elems = (size_t)nw * ldm;
   float2* gbufs = stage_base + nbuf * stage_elems;
-  int* sL_base = reinterpret_cast<int*>(gbufs + kWarps * TPW * GB);
+  float2* tws = gbufs + kWarps * TPW * GB;  // the lanes' twiddle factors
+  int* sL_base = reinterpret_cast<int*>(tws + kLaneTw * P);
+  for (int i = threadIdx.x; i < kLaneTw * P; i += kThreads) tws[i] = lane_twiddle_entry<NT>(s.twl, i / P, i % P);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / P, p = lane % P;
@@ -496,7 +502,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       });
 
       // 2. inverse transform: z_n = x(2n) + i x(2n+1) up to the factor 1/nt
-      group_fft<NT, true>(v, gbuf, p, s.twl);
+      group_fft<NT, true>(v, gbuf, p, tws);
 
       // 3. y = theta s on the window samples of this lane (the rest is zero),
       //    its energy, and f1 on the window: even iterations
@@ -563,7 +569,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       const float esum = (eq[0] + eq[1]) + (eq[2] + eq[3]);
 
       // 5. forward transform of y
-      group_fft<NT, false>(w, gbuf, p, s.twl);
+      group_fft<NT, false>(w, gbuf, p, tws);
 
       // 6. post-processing for the band bins k = q + P e' < nw: the partner
       //    Zf_{(M-k) mod M} comes from lane (P - q) mod P of the group

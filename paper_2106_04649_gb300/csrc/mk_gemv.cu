@@ -174,11 +174,16 @@ constexpr int kUnitRows = 64;  // rows per work unit, all of one frequency (8 st
 // count; a stage without rows ends the stream.  The last CTA to finish
 // resets the counters (queue[0]: next unit, queue[1]: finished CTAs), so
 // every launch starts from zero; no thread leaves before the final barrier.
-template <int PER>
+//
+// FV > 1 (a few focal points): each row of R meets the spectra of nf <= FV
+// focal points (Nw rows f = 0 .. nf-1 of the pass, rq float4 apart) in one
+// pass, with the F = 1 arithmetic per focal point; outputs go to column
+// f * ns + k of S.
+template <int PER, int FV>
 __global__ void __launch_bounds__(kBulkThreads, 1)
 gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, float2* __restrict__ S, int ns,
                  int rq, int64_t nw_stride4, int64_t s_stride, float c, int nw, int stages,
-                 unsigned* __restrict__ queue, int* __restrict__ err) {
+                 unsigned* __restrict__ queue, int* __restrict__ err, int nf) {
   extern __shared__ __align__(128) float4 ring[];
   __shared__ __align__(8) uint64_t full_bar[kMaxStages];
   __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
@@ -250,7 +255,7 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
     // may already be under way.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     int cur_w = -1;
-    float4 nv[PER];
+    float4 nv[FV][PER];
     for (uint32_t it = 0;; ++it) {
       const int s = (int)(it % stages);
       const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&full_bar[s]), (it / stages) & 1u));
@@ -267,33 +272,46 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
         if (w != cur_w) {
           const float4* nrow = Nw + (int64_t)w * nw_stride4;
 #pragma unroll
-          for (int q = 0; q < PER; ++q) {
-            const int i = lane + 32 * q;
-            nv[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-          }
+          for (int f = 0; f < FV; ++f)
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+              const int i = lane + 32 * q;
+              nv[f][q] = i < rq && f < nf ? __ldg(nrow + (int64_t)f * rq + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
           cur_w = w;
         }
         const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
-        float re = 0.f, im = 0.f;
+        float re[FV], im[FV];
+#pragma unroll
+        for (int f = 0; f < FV; ++f) re[f] = im[f] = 0.f;
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
           const int i = lane + 32 * q;
           const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-          re = fmaf(rv.x, nv[q].x, re);
-          re = fmaf(-rv.y, nv[q].y, re);
-          re = fmaf(rv.z, nv[q].z, re);
-          re = fmaf(-rv.w, nv[q].w, re);
-          im = fmaf(rv.x, nv[q].y, im);
-          im = fmaf(rv.y, nv[q].x, im);
-          im = fmaf(rv.z, nv[q].w, im);
-          im = fmaf(rv.w, nv[q].z, im);
+#pragma unroll
+          for (int f = 0; f < FV; ++f) {
+            re[f] = fmaf(rv.x, nv[f][q].x, re[f]);
+            re[f] = fmaf(-rv.y, nv[f][q].y, re[f]);
+            re[f] = fmaf(rv.z, nv[f][q].z, re[f]);
+            re[f] = fmaf(-rv.w, nv[f][q].w, re[f]);
+            im[f] = fmaf(rv.x, nv[f][q].y, im[f]);
+            im[f] = fmaf(rv.y, nv[f][q].x, im[f]);
+            im[f] = fmaf(rv.z, nv[f][q].w, im[f]);
+            im[f] = fmaf(rv.w, nv[f][q].z, im[f]);
+          }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          re += __shfl_xor_sync(0xffffffffu, re, o);
-          im += __shfl_xor_sync(0xffffffffu, im, o);
+        for (int f = 0; f < FV; ++f)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            re[f] += __shfl_xor_sync(0xffffffffu, re[f], o);
+            im[f] += __shfl_xor_sync(0xffffffffu, im[f], o);
+          }
+        if (lane == 0) {
+#pragma unroll
+          for (int f = 0; f < FV; ++f)
+            if (f < nf) S[(int64_t)w * s_stride + (int64_t)f * ns + k] = make_float2(c * re[f], c * im[f]);
         }
-        if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
@@ -315,8 +333,8 @@ int bulk_stages(int rq) {
   return st > kMaxStages ? kMaxStages : st;
 }
 
-template <int PER>
-cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
+template <int PER, int FV>
+cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms, int f0, int nf) {
   const int rq = s.r_pad / 2;
   const int stages = bulk_stages(rq);
   const size_t smem = (size_t)stages * kConsWarps * rq * 16;
@@ -338,14 +356,38 @@ cudaError_t launch_bulk_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = s.pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, gemv_bulk_kernel<PER>, reinterpret_cast<const float4*>(s.R),
-                            reinterpret_cast<const float4*>(s.Nw), s.S, s.ns, rq, s.nw_stride / 2, s.s_stride, s.c,
-                            s.nw, stages, s.counter + 1, s.err);
+  return cudaLaunchKernelEx(&cfg, gemv_bulk_kernel<PER, FV>, reinterpret_cast<const float4*>(s.R),
+                            reinterpret_cast<const float4*>(s.Nw) + (int64_t)f0 * rq, s.S + (int64_t)f0 * s.ns,
+                            s.ns, rq, s.nw_stride / 2, s.s_stride, s.c, s.nw, stages, s.counter + 1, s.err, nf);
 }
 
-template <int PER>
+template <int PER, int FV>
 cudaError_t set_bulk_attr() {
-  return cudaFuncSetAttribute(gemv_bulk_kernel<PER>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+  return cudaFuncSetAttribute(gemv_bulk_kernel<PER, FV>, cudaFuncAttributeMaxDynamicSharedMemorySize, kRingBytes);
+}
+
+// Focal points per pass of R: 1 for F = 1; else 4 where the field slices fit
+// in registers (PER <= 6), else 2.
+int focal_per_pass(int F, int per) { return F == 1 ? 1 : (F > 2 && per <= 6 ? 4 : 2); }
+
+template <int PER>
+cudaError_t launch_bulk(const SurveyDev& s, cudaStream_t st, int num_sms) {
+  const int fv = focal_per_pass(s.F, PER);
+  for (int f0 = 0; f0 < s.F; f0 += fv) {
+    const int nf = s.F - f0 < fv ? s.F - f0 : fv;
+    cudaError_t e;
+    if (fv == 1) {
+      e = launch_bulk_per<PER, 1>(s, st, num_sms, f0, nf);
+    } else if constexpr (PER <= 6) {
+      e = fv == 4 ? launch_bulk_per<PER, 4>(s, st, num_sms, f0, nf) : launch_bulk_per<PER, 2>(s, st, num_sms, f0, nf);
+    } else if constexpr (PER <= 12) {
+      e = launch_bulk_per<PER, 2>(s, st, num_sms, f0, nf);
+    } else {
+      e = cudaErrorNotSupported;  // gemv_takes() keeps these surveys off the multi-focal form
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <int PER>
@@ -367,28 +409,38 @@ cudaError_t launch_gemv_per(const SurveyDev& s, cudaStream_t st, int num_sms) {
 
 cudaError_t prepare_gemv() {
   cudaError_t e;
-#define MK_BULK_ATTR(P) \
-  if ((e = set_bulk_attr<P>()) != cudaSuccess) return e;
-  MK_BULK_ATTR(1) MK_BULK_ATTR(2) MK_BULK_ATTR(4) MK_BULK_ATTR(6) MK_BULK_ATTR(8) MK_BULK_ATTR(10) MK_BULK_ATTR(12)
-  MK_BULK_ATTR(16) MK_BULK_ATTR(20)
+#define MK_BULK_ATTR(P, V) \
+  if ((e = set_bulk_attr<P, V>()) != cudaSuccess) return e;
+  MK_BULK_ATTR(1, 1) MK_BULK_ATTR(2, 1) MK_BULK_ATTR(4, 1) MK_BULK_ATTR(6, 1) MK_BULK_ATTR(8, 1) MK_BULK_ATTR(10, 1)
+  MK_BULK_ATTR(12, 1) MK_BULK_ATTR(16, 1) MK_BULK_ATTR(20, 1)
+  MK_BULK_ATTR(1, 2) MK_BULK_ATTR(2, 2) MK_BULK_ATTR(4, 2) MK_BULK_ATTR(6, 2) MK_BULK_ATTR(8, 2) MK_BULK_ATTR(10, 2)
+  MK_BULK_ATTR(12, 2) MK_BULK_ATTR(1, 4) MK_BULK_ATTR(2, 4) MK_BULK_ATTR(4, 4) MK_BULK_ATTR(6, 4)
 #undef MK_BULK_ATTR
   return cudaSuccess;
+}
+
+bool gemv_takes(const SurveyDev& s) {
+  if (s.F == 1) return true;
+  const int rq = s.r_pad / 2;
+  const int per = (rq + 31) / 32;
+  return s.F <= kGemvMaxFocal && per <= 12 && bulk_stages(rq) >= 2;
 }
 
 cudaError_t launch_gemv(const SurveyDev& s, cudaStream_t st, int num_sms) {
   const int rq = s.r_pad / 2;
   const int per = (rq + 31) / 32;
+  if (s.F > 1 && !gemv_takes(s)) return cudaErrorNotSupported;
   if (per <= 20 && bulk_stages(rq) >= 2) {
     switch (per) {
-      case 1: return launch_bulk_per<1>(s, st, num_sms);
-      case 2: return launch_bulk_per<2>(s, st, num_sms);
-      case 3: case 4: return launch_bulk_per<4>(s, st, num_sms);
-      case 5: case 6: return launch_bulk_per<6>(s, st, num_sms);
-      case 7: case 8: return launch_bulk_per<8>(s, st, num_sms);
-      case 9: case 10: return launch_bulk_per<10>(s, st, num_sms);
-      case 11: case 12: return launch_bulk_per<12>(s, st, num_sms);
-      case 13: case 14: case 15: case 16: return launch_bulk_per<16>(s, st, num_sms);
-      default: return launch_bulk_per<20>(s, st, num_sms);
+      case 1: return launch_bulk<1>(s, st, num_sms);
+      case 2: return launch_bulk<2>(s, st, num_sms);
+      case 3: case 4: return launch_bulk<4>(s, st, num_sms);
+      case 5: case 6: return launch_bulk<6>(s, st, num_sms);
+      case 7: case 8: return launch_bulk<8>(s, st, num_sms);
+      case 9: case 10: return launch_bulk<10>(s, st, num_sms);
+      case 11: case 12: return launch_bulk<12>(s, st, num_sms);
+      case 13: case 14: case 15: case 16: return launch_bulk<16>(s, st, num_sms);
+      default: return launch_bulk<20>(s, st, num_sms);
     }
   }
   switch (per) {

@@ -67,6 +67,13 @@ struct SurveyDev {
                       // the epilogue when it reads S
 };
 
+#ifdef __CUDACC__
+// bytes [a, a + n) into L2 (a 16-byte aligned, n a multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void* a, unsigned n) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"(n) : "memory");
+}
+#endif
+
 // Storage precisions whose epilogue writes the complex FP32 field spectrum Nw
 // (complex FP32 R, and the scaled FP16 split, which quantises Nw at each
 // contraction); the other 16-bit forms write their embedding directly.
@@ -133,6 +140,11 @@ cudaError_t prepare_kernels();  // one-time function attributes (large dynamic s
 cudaError_t prepare_contract();  // called by prepare_kernels
 cudaError_t prepare_gemv();
 cudaError_t launch_gemv(const SurveyDev& s, cudaStream_t st, int num_sms);
+// Complex FP32 R with a few focal points (F <= kGemvMaxFocal): the GEMV takes
+// 2 or 4 of them per pass over R (memory-bound) where a GEMM tile of 64
+// columns would compute mostly padding.
+constexpr int kGemvMaxFocal = 8;
+bool gemv_takes(const SurveyDev& s);
 cudaError_t launch_cgemm_simt(const SurveyDev& s, cudaStream_t st);
 void set_noplan_error(const char* msg);  // message returned by mk_last_error(NULL)
 

@@ -1,6 +1,6 @@
 """Large survey: 4001 x 4001 positions, nt = 4096, 984 kept bins, one focal
 batch of 32 points of the 4001-point line, R held as 3-way split BF16
-(2 x 95 GB).  FP64 R at this size is 252 GB, so the oracle follows sampled
+(3 x 63 GB) or as the scaled FP16 split (2 x 63 GB).  FP64 R at this size is 252 GB, so the oracle follows sampled
 focal points through the series with R rebuilt element by element from the
 generator's factors (``synthesis_factored``, a plain C contraction):
 
@@ -20,18 +20,19 @@ from tests.helpers import desc_for
 
 pytestmark = pytest.mark.gpu
 
-SPLIT3 = 4
+SPLIT3, SPLIT_F16 = 4, 5
 TOL_ACC = 1e-5   # accumulated fields (rel L2)
 TOL_N = 1e-4     # the current N_i
 
 
-def test_large_series_sampled_focal_points_and_linearity():
+@pytest.mark.parametrize("rprec", [SPLIT3, SPLIT_F16], ids=["split3", "splitf16"])
+def test_large_series_sampled_focal_points_and_linearity(rprec):
     import torch
     from paper_2106_04649_gb300 import _native as N
     from paper_2106_04649_gb300.api import Plan
     from synthetic.torch_gen import reflection_band_chunks
     s = S.large_survey(nfocal=32)
-    plan = Plan([desc_for(s, rprec=SPLIT3)])
+    plan = Plan([desc_for(s, rprec=rprec)])
     for w0, blk in reflection_band_chunks(s, "cuda", chunk=4):
         plan.load_R(0, blk.contiguous(), w_begin=w0)
     torch.cuda.synchronize()

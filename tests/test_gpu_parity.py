@@ -401,3 +401,23 @@ def test_register_epilogue_shapes(nt, dt, fmax, rprec):
         _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"nt={nt} rprec={rprec} iter {i}")
         assert np.max(np.abs(e[0] - hist[i].energy[i]) / hist[i].energy[i]) <= TOL_E
     p.close()
+
+
+@pytest.mark.parametrize("n,F", [(25, 5), (75, 8), (300, 5), (500, 2), (500, 5), (75, 9)])
+def test_few_focal_points_complex_fp32(n, F):
+    # complex FP32 R with 2 .. 8 focal points: the GEMV takes 4 of them per pass
+    # over R where their field slices fit in registers (rows of at most 384
+    # positions), else 2, with a ragged last pass (F = 5); F = 9 is the first
+    # count that runs the SIMT GEMM.  Per iteration against the oracle.
+    from paper_2106_04649_gb300.api import Plan
+    s = _many_focal(n, 128, 0.008, F, 40.0)
+    R, td, Gd = survey_inputs(s)
+    _, hist = M.run(R.astype(np.complex128), Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 4, history=True)
+    p = Plan([desc_for(s)])
+    p.load_R(0, R)
+    p.set_Gd_window(0, Gd, td, s.eps)
+    for i in range(4):
+        e = p.iterate(1)
+        _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"n={n} F={F} iter {i}")
+        assert np.max(np.abs(e[0] - hist[i].energy[i]) / hist[i].energy[i]) <= TOL_E
+    p.close()

@@ -52,7 +52,7 @@ def _exchange(plans, bounds):
 
 @pytest.mark.parametrize("n,nt,F,fmax,rprec,bounds", [
     (40, 128, 1, None, 0, [(0, 32), (32, 40)]),                 # F = 1: GEMV, pmin spectrum
-    (75, 128, 3, 40.0, 0, [(0, 32), (32, 64), (64, 75)]),       # SIMT complex GEMM, three shards
+    (75, 128, 3, 40.0, 0, [(0, 32), (32, 64), (64, 75)]),       # GEMV, 3 focal points per pass, three shards
     (75, 256, 3, None, 4, [(0, 64), (64, 75)]),                 # tcgen05, 3-way split embedding
     (70, 128, 2, 40.0, 1, [(0, 32), (32, 70)]),                 # tcgen05, BF16 R
     (75, 1024, 80, 30.0, 0, [(0, 32), (32, 64), (64, 75)]),     # register epilogue on the full shards
