@@ -1,5 +1,7 @@
 // The contraction of Eq. (1) for one focal point: a complex GEMV per frequency,
-// S_m(k) = c * sum_r R_m(k, r) Nw_m(r), bound by HBM bandwidth.
+// S_m(k) = c * sum_r R_m(k, r) Nw_m(r), bound by HBM bandwidth; for a few
+// focal points (complex FP32 R, F <= 8) the same kernel takes 2 or 4 of them
+// per pass over R.
 //
 // Paper, Implementation section: the space integral over the fastest axis of
 // R is a segmented dot product (pointwise product followed by a segmented
