@@ -257,7 +257,8 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
     // may already be under way.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     int cur_w = -1;
-    float4 nv[FV][PER];
+    float4 nv1[PER];
+    float4 nv[FV > 1 ? FV : 1][FV > 1 ? PER : 1];
     for (uint32_t it = 0;; ++it) {
       const int s = (int)(it % stages);
       const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_u32(&full_bar[s]), (it / stages) & 1u));
@@ -271,48 +272,81 @@ gemv_bulk_kernel(const float4* __restrict__ R, const float4* __restrict__ Nw, fl
         const int64_t row = row0 + warp;
         const int w = (int)(row / ns);
         const int k = (int)(row - (int64_t)w * ns);
-        if (w != cur_w) {
-          const float4* nrow = Nw + (int64_t)w * nw_stride4;
-#pragma unroll
-          for (int f = 0; f < FV; ++f)
+        if constexpr (FV == 1) {
+          if (w != cur_w) {
+            const float4* nrow = Nw + (int64_t)w * nw_stride4;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
               const int i = lane + 32 * q;
-              nv[f][q] = i < rq && f < nf ? __ldg(nrow + (int64_t)f * rq + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+              nv1[q] = i < rq ? __ldg(nrow + i) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-          cur_w = w;
-        }
-        const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
-        float re[FV], im[FV];
-#pragma unroll
-        for (int f = 0; f < FV; ++f) re[f] = im[f] = 0.f;
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-          const int i = lane + 32 * q;
-          const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-          for (int f = 0; f < FV; ++f) {
-            re[f] = fmaf(rv.x, nv[f][q].x, re[f]);
-            re[f] = fmaf(-rv.y, nv[f][q].y, re[f]);
-            re[f] = fmaf(rv.z, nv[f][q].z, re[f]);
-            re[f] = fmaf(-rv.w, nv[f][q].w, re[f]);
-            im[f] = fmaf(rv.x, nv[f][q].y, im[f]);
-            im[f] = fmaf(rv.y, nv[f][q].x, im[f]);
-            im[f] = fmaf(rv.z, nv[f][q].w, im[f]);
-            im[f] = fmaf(rv.w, nv[f][q].z, im[f]);
+            cur_w = w;
           }
-        }
+          const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
+          float re = 0.f, im = 0.f;
 #pragma unroll
-        for (int f = 0; f < FV; ++f)
+          for (int q = 0; q < PER; ++q) {
+            const int i = lane + 32 * q;
+            const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+            re = fmaf(rv.x, nv1[q].x, re);
+            re = fmaf(-rv.y, nv1[q].y, re);
+            re = fmaf(rv.z, nv1[q].z, re);
+            re = fmaf(-rv.w, nv1[q].w, re);
+            im = fmaf(rv.x, nv1[q].y, im);
+            im = fmaf(rv.y, nv1[q].x, im);
+            im = fmaf(rv.z, nv1[q].w, im);
+            im = fmaf(rv.w, nv1[q].z, im);
+          }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            re[f] += __shfl_xor_sync(0xffffffffu, re[f], o);
-            im[f] += __shfl_xor_sync(0xffffffffu, im[f], o);
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
           }
-        if (lane == 0) {
+          if (lane == 0) S[(int64_t)w * s_stride + k] = make_float2(c * re, c * im);
+        } else {
+          if (w != cur_w) {
+            const float4* nrow = Nw + (int64_t)w * nw_stride4;
+#pragma unroll
+            for (int f = 0; f < FV; ++f)
+#pragma unroll
+              for (int q = 0; q < PER; ++q) {
+                const int i = lane + 32 * q;
+                nv[f][q] = i < rq && f < nf ? __ldg(nrow + (int64_t)f * rq + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+              }
+            cur_w = w;
+          }
+          const float4* rr = ring + (size_t)s * stage_f4 + (size_t)warp * rq;
+          float re[FV], im[FV];
+#pragma unroll
+          for (int f = 0; f < FV; ++f) re[f] = im[f] = 0.f;
+#pragma unroll
+          for (int q = 0; q < PER; ++q) {
+            const int i = lane + 32 * q;
+            const float4 rv = i < rq ? rr[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int f = 0; f < FV; ++f) {
+              re[f] = fmaf(rv.x, nv[f][q].x, re[f]);
+              re[f] = fmaf(-rv.y, nv[f][q].y, re[f]);
+              re[f] = fmaf(rv.z, nv[f][q].z, re[f]);
+              re[f] = fmaf(-rv.w, nv[f][q].w, re[f]);
+              im[f] = fmaf(rv.x, nv[f][q].y, im[f]);
+              im[f] = fmaf(rv.y, nv[f][q].x, im[f]);
+              im[f] = fmaf(rv.z, nv[f][q].w, im[f]);
+              im[f] = fmaf(rv.w, nv[f][q].z, im[f]);
+            }
+          }
 #pragma unroll
           for (int f = 0; f < FV; ++f)
-            if (f < nf) S[(int64_t)w * s_stride + (int64_t)f * ns + k] = make_float2(c * re[f], c * im[f]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              re[f] += __shfl_xor_sync(0xffffffffu, re[f], o);
+              im[f] += __shfl_xor_sync(0xffffffffu, im[f], o);
+            }
+          if (lane == 0) {
+#pragma unroll
+            for (int f = 0; f < FV; ++f)
+              if (f < nf) S[(int64_t)w * s_stride + (int64_t)f * ns + k] = make_float2(c * re[f], c * im[f]);
+          }
         }
       }
       __syncwarp();
