@@ -21,9 +21,13 @@
 // transpose through a shared buffer private to the group, and 32/P DFTs of
 // P points in registers.  The result comes back in the same index layout
 // (k = q + P e'), so the inverse transform's output feeds the forward
-// transform directly.  Constant twiddles are compile-time 64th roots of
-// unity; per-lane twiddles are products of two entries of a table of
-// e^{-2 pi i j / nt} (FP64 values rounded to FP32), loaded once per lane.
+// transform directly.  For nt = 4096 (P = 64) a trace takes two warps: the
+// 64-point DFTs over the lanes split by decimation in frequency into a
+// butterfly across the two warps (through the group's shared buffer, the
+// warps meeting at a named barrier) and 32-point DFTs in registers.
+// Constant twiddles are compile-time 64th roots of unity; per-lane twiddles
+// are products of two entries of a table of e^{-2 pi i j / nt} (FP64 values
+// rounded to FP32), kept in shared memory per CTA.
 //
 // A CTA of 8 warps takes blocks of consecutive traces (focal-major order, so
 // neighbouring traces are neighbouring addresses in S and Nw): the block's
@@ -46,7 +50,6 @@ namespace {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
-constexpr size_t kSmemMax = 220 * 1024;
 
 // cos(2 pi r / 64), r = 0 .. 16 (FP64 values rounded to FP32)
 __host__ __device__ constexpr float qcos(int r) {
@@ -183,12 +186,14 @@ __host__ __device__ __forceinline__ void dft(float2 (&v)[N]) {
 template <int P>
 __host__ __device__ constexpr int out_e(int a) { return a / P + (32 / P) * (a % P); }
 template <int P>
-__host__ __device__ constexpr int out_slot(int e) { return (e % (32 / P)) * P + e / (32 / P); }
+__host__ __device__ constexpr int out_slot(int e) { return P >= 32 ? e : (e % (32 / P)) * P + e / (32 / P); }
 
 // Shared buffer of one trace group (float2 elements): the 32 x P transpose,
 // rows of P + 1; for P < 16 the groups sharing a half-warp are staggered by
 // P elements so that their accesses hit disjoint banks.  One lane per trace
-// (P = 1) needs no transpose.
+// (P = 1) needs no transpose.  For P = 64 (two warps per trace) the buffer
+// also carries the post-processing exchange (M values) and, past them, the
+// second warp's energy partial.
 template <int P>
 __host__ __device__ constexpr int group_buf() { return P == 1 ? 0 : 32 * (P + 1) + (P < 16 ? P : 0); }
 
@@ -211,13 +216,57 @@ __device__ __forceinline__ void lane_twiddles(const float2* tws, int p, float2 (
   for (int a = 1; a < 4; ++a) wa[a] = tws[(6 + a) * P + p];
 }
 
+// The two warps of a P = 64 group meet at named barrier bar (1 + group).
+__device__ __forceinline__ void pair_sync(int bar) { asm volatile("bar.sync %0, 64;" ::"r"(bar) : "memory"); }
+
 // Complex DFT of M = 32 P points over the P lanes of a group (lane p holds
 // n = p + P e at v[e]); afterwards lane q holds index k = q + P out_e(a) at
-// v[a].  gbuf is the group's shared buffer (half the transpose per pass).
+// v[a].  gbuf is the group's shared buffer.
+//
+// P = 64 (nt = 4096, two warps per trace): after the 32-point DFTs over e
+// and the twiddles W_M^{p k2}, the 64-point DFTs over p run split by
+// decimation in frequency, k1 = 2j + h: lane (h, k2) of warp h forms
+// u_p = (x_p + (-1)^h x_{p+32}) W_64^{p h}, p < 32, from the transposed
+// values and takes its 32-point DFT, so that lane q = 32h + k2 ends with
+// index k = q + 64 j at v[j].  Both warps call this with the same bar.
 template <int NT, bool INV>
-__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, const float2* tws) {
+__device__ __forceinline__ void group_fft(float2 (&v)[32], float2* gbuf, int p, const float2* tws, int bar) {
   constexpr int P = NT / 64;
-  if constexpr (P > 1) {
+  if constexpr (P == 64) {
+    float2 wa[4], wb[8];
+    lane_twiddles<NT>(tws, p, wa, wb);
+    dft<32, INV>(v);  // over e: v[k2]
+    static_for<32>([&](auto K) {
+      constexpr int k2 = decltype(K)::value;
+      constexpr int a = k2 >> 3, b = k2 & 7;
+      if constexpr (k2 > 0) {
+        float2 w;
+        if constexpr (a == 0) {
+          w = wb[b];
+        } else if constexpr (b == 0) {
+          w = wa[a];
+        } else {
+          w = cmul(wa[a], wb[b]);
+        }
+        v[k2] = INV ? cmulc(v[k2], w) : cmul(v[k2], w);
+      }
+    });
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) gbuf[k2 * 65 + p] = v[k2];
+    pair_sync(bar);
+    const float2* row = gbuf + (p & 31) * 65;  // k2 = p mod 32
+    if (p >= 32) {
+      static_for<32>([&](auto Q) {
+        constexpr int q = decltype(Q)::value;
+        v[q] = rot64<q, INV>(csub(row[q], row[q + 32]));
+      });
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = cadd(row[q], row[q + 32]);
+    }
+    pair_sync(bar);  // the buffer is free again
+    dft<32, INV>(v);
+  } else if constexpr (P > 1) {
     float2 wa[4], wb[8];
     lane_twiddles<NT>(tws, p, wa, wb);
     dft<32, INV>(v);  // over e: v[k2]
@@ -286,15 +335,16 @@ struct EpiShape {
 constexpr int kCtasPerSm = 2;
 constexpr size_t kSmemPerCta = 110 * 1024;  // two CTAs per SM
 
+// traces a CTA transforms at once (one per group of P = nt/64 lanes)
 template <int NT>
-__host__ __device__ constexpr int traces_per_warp() { return 32 / (NT / 64); }
+__host__ __device__ constexpr int traces_per_cta() { return kThreads / (NT / 64); }
 
 template <int NT>
 size_t epi_smem(int nw, int rounds, int nbuf) {
   constexpr int P = NT / 64;
-  const int bt = kWarps * traces_per_warp<NT>() * rounds;
+  const int bt = traces_per_cta<NT>() * rounds;
   return (size_t)nbuf * nw * (bt + 1) * sizeof(float2) +
-         (size_t)kWarps * traces_per_warp<NT>() * group_buf<P>() * sizeof(float2) +
+         (size_t)traces_per_cta<NT>() * group_buf<P>() * sizeof(float2) +
          (size_t)kLaneTw * P * sizeof(float2) + (size_t)nbuf * bt * sizeof(int);
 }
 
@@ -356,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, int nbuf) {
   constexpr int M = NT / 2;
   constexpr int P = NT / 64;
-  constexpr int TPW = 32 / P;
+  constexpr int NG = kThreads / P;  // trace groups per CTA
   constexpr int GB = group_buf<P>();
   extern __shared__ float4 smem_raw[];
   __shared__ int s_last;
@@ -365,19 +415,19 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
   // complete before it reads what this grid writes
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
-  const int bt = kWarps * TPW * rounds;
+  const int bt = NG * rounds;
   const int ldm = bt + 1;
   const int nw = s.nw;
   float2* stage_base = reinterpret_cast<float2*>(smem_raw);
   const size_t stage_elems = (size_t)nw * ldm;
   float2* gbufs = stage_base + nbuf * stage_elems;
-  float2* tws = gbufs + kWarps * TPW * GB;  // the lanes' twiddle factors
+  float2* tws = gbufs + NG * GB;  // the lanes' twiddle factors
   int* sL_base = reinterpret_cast<int*>(tws + kLaneTw * P);
   for (int i = threadIdx.x; i < kLaneTw * P; i += kThreads) tws[i] = lane_twiddle_entry<NT>(s.twl, i / P, i % P);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int grp = lane / P, p = lane % P;
-  float2* gbuf = gbufs + (warp * TPW + grp) * GB;
+  const int slot = (int)threadIdx.x / P, p = (int)threadIdx.x % P;  // trace group, lane in the group
+  float2* gbuf = gbufs + slot * GB;
   float2 up;  // e^{+2 pi i p / nt}
   {
     const float2 w = __ldg(s.twl + p);
@@ -453,7 +503,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
     }
 
     for (int r = 0; r < rounds; ++r) {
-      const int c = r * (kWarps * TPW) + warp * TPW + grp;  // stage column of this group's trace
+      const int c = r * NG + slot;  // stage column of this group's trace
       const bool active = c < ntr;
       const int L = active ? sL[c] : 0;
       float* __restrict__ ft = f1 + (int64_t)(tb + (active ? c : 0)) * NT;  // this trace of f1
@@ -502,7 +552,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       });
 
       // 2. inverse transform: z_n = x(2n) + i x(2n+1) up to the factor 1/nt
-      group_fft<NT, true>(v, gbuf, p, tws);
+      group_fft<NT, true>(v, gbuf, p, tws, 1 + slot);
 
       // 3. y = theta s on the window samples of this lane (the rest is zero),
       //    its energy, and f1 on the window: even iterations
@@ -569,7 +619,7 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       const float esum = (eq[0] + eq[1]) + (eq[2] + eq[3]);
 
       // 5. forward transform of y
-      group_fft<NT, false>(w, gbuf, p, tws);
+      group_fft<NT, false>(w, gbuf, p, tws, 1 + slot);
 
       // 6. post-processing for the band bins k = q + P e' < nw: the partner
       //    Zf_{(M-k) mod M} comes from lane (P - q) mod P of the group
@@ -577,16 +627,46 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
       //    (32 - e') mod 32.  Y_k = E_k + e^{-2 pi i k/nt} O_k with
       //    E_k = (Zf_k + conj Zf_{M-k})/2, O_k = (Zf_k - conj Zf_{M-k})/(2i);
       //    the band spectrum of N_i is -conj(Y_k).
-      const int src = (P - p) & (P - 1);
+      //    For P = 64 the partners sit in the other warp: the group's Zf
+      //    pass through its buffer, and so does the second warp's energy sum.
+      // the lanes' energy sums of this warp, combined error-free
+      auto warp_energy = [&](float& hi, float& lo) {
+        constexpr int WD = P < 32 ? P : 32;
+        hi = esum;
+        lo = 0.f;
+#pragma unroll
+        for (int o = WD / 2; o > 0; o >>= 1) {
+          const float h2 = __shfl_down_sync(0xffffffffu, hi, o, WD);
+          const float l2 = __shfl_down_sync(0xffffffffu, lo, o, WD);
+          float sum, err;
+          two_sum(hi, h2, sum, err);
+          hi = sum;
+          lo = lo + l2 + err;
+        }
+      };
+      float hi = 0.f, lo = 0.f;
+      if constexpr (P == 64) {
+        warp_energy(hi, lo);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) gbuf[p + 64 * e] = w[e];
+        if (p == 32) gbuf[M] = make_float2(hi, lo);
+        pair_sync(1 + slot);
+      }
       static_for<32>([&](auto Ee) {
         constexpr int e = decltype(Ee)::value;
         if (e * P < nw) {  // uniform: some lane of every group has k < nw
-          const float2 offer = w[out_slot<P>(31 - e)];
-          float2 got;
-          got.x = __shfl_sync(0xffffffffu, offer.x, src, P);
-          got.y = __shfl_sync(0xffffffffu, offer.y, src, P);
           const float2 Z = w[out_slot<P>(e)];
-          const float2 pz = p != 0 ? got : w[out_slot<P>((32 - e) & 31)];
+          float2 pz;
+          if constexpr (P == 64) {
+            pz = gbuf[(M - (p + 64 * e)) & (M - 1)];
+          } else {
+            const int src = (P - p) & (P - 1);
+            const float2 offer = w[out_slot<P>(31 - e)];
+            float2 got;
+            got.x = __shfl_sync(0xffffffffu, offer.x, src, P);
+            got.y = __shfl_sync(0xffffffffu, offer.y, src, P);
+            pz = p != 0 ? got : w[out_slot<P>((32 - e) & 31)];
+          }
           if (e < ek) {
             const float2 Zc = make_float2(pz.x, -pz.y);
             const float2 Ev = make_float2(0.5f * (Z.x + Zc.x), 0.5f * (Z.y + Zc.y));
@@ -601,16 +681,19 @@ epi_warp_kernel(SurveyDev s, double* __restrict__ ring, int slots, int rounds, i
         col[M * ldm] = make_float2(-(w[0].x - w[0].y), 0.f);
       }
 
-      // 7. the trace's energy: lanes combined error-free in FP32, then FP64
-      float hi = esum, lo = 0.f;
-#pragma unroll
-      for (int o = P / 2; o > 0; o >>= 1) {
-        const float h2 = __shfl_down_sync(0xffffffffu, hi, o, P);
-        const float l2 = __shfl_down_sync(0xffffffffu, lo, o, P);
-        float sum, err;
-        two_sum(hi, h2, sum, err);
-        hi = sum;
-        lo = lo + l2 + err;
+      // 7. the trace's energy: lanes combined error-free in FP32 (for P = 64
+      //    the second warp's sum joins through the group buffer), then FP64
+      if constexpr (P < 64) {
+        warp_energy(hi, lo);
+      } else {
+        if (p == 0) {
+          const float2 o2 = gbuf[M];
+          float sum, err;
+          two_sum(hi, o2.x, sum, err);
+          hi = sum;
+          lo = lo + o2.y + err;
+        }
+        pair_sync(1 + slot);  // the buffer is free again
       }
       if (active && p == 0) s.Epart[tb + c] = (double)hi + (double)lo;
     }
@@ -686,14 +769,14 @@ bool epi_shape(const SurveyDev& s, int num_sms, EpiShape* out) {
     rounds = s.epi_g >= 2 ? 2 : 1;
   } else {
     // few traces: one round per block, so that more SMs get blocks
-    const int bt2 = kWarps * traces_per_warp<NT>() * 2;
+    const int bt2 = traces_per_cta<NT>() * 2;
     if (s.F * ((s.ns + bt2 - 1) / bt2) < kCtasPerSm * num_sms) rounds = 1;
   }
   for (; rounds >= 1; --rounds) {
     for (int nbuf = 2; nbuf >= 1; --nbuf) {
       const size_t smem = epi_smem<NT>(s.nw, rounds, nbuf);
       if (smem <= kSmemPerCta) {
-        *out = {rounds, nbuf, kWarps * traces_per_warp<NT>() * rounds, smem};
+        *out = {rounds, nbuf, traces_per_cta<NT>() * rounds, smem};
         return true;
       }
     }
@@ -730,6 +813,7 @@ bool epilogue_warp_supports(int nt, int nw) {
     case 512: return epi_shape<512>(s, 1, &sh);
     case 1024: return epi_shape<1024>(s, 1, &sh);
     case 2048: return epi_shape<2048>(s, 1, &sh);
+    case 4096: return epi_shape<4096>(s, 1, &sh);
     default: return false;
   }
 }
@@ -741,7 +825,8 @@ cudaError_t prepare_epilogue_warp() {
   if ((e = set_attr<256>()) != cudaSuccess) return e;
   if ((e = set_attr<512>()) != cudaSuccess) return e;
   if ((e = set_attr<1024>()) != cudaSuccess) return e;
-  return set_attr<2048>();
+  if ((e = set_attr<2048>()) != cudaSuccess) return e;
+  return set_attr<4096>();
 }
 
 cudaError_t launch_epilogue_warp(const SurveyDev& s, double* ring, int slots, cudaStream_t st, int num_sms) {
@@ -752,6 +837,7 @@ cudaError_t launch_epilogue_warp(const SurveyDev& s, double* ring, int slots, cu
     case 512: return launch_nt<512>(s, ring, slots, st, num_sms);
     case 1024: return launch_nt<1024>(s, ring, slots, st, num_sms);
     case 2048: return launch_nt<2048>(s, ring, slots, st, num_sms);
+    case 4096: return launch_nt<4096>(s, ring, slots, st, num_sms);
     default: return cudaErrorNotSupported;
   }
 }

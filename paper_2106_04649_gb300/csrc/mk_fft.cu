@@ -951,7 +951,14 @@ cudaError_t launch_set_iter(const SurveyDev& s, int value, cudaStream_t st) {
 // (one block of up to 8 traces per CTA, two CTAs per SM); with fewer each warp
 // holds a single trace and the shared-memory epilogue, whose 256 threads share
 // a pair of traces, finishes sooner.
+// At nt = 4096 a register-epilogue block holds 4 traces (shared memory), so
+// the 16-bit embedding's row segments are 16-byte halves of 32-byte sectors;
+// there the shared-memory epilogue, whose blocks hold 8 traces, is faster
+// (4001 positions, 128 focal points, 3-way split: 25.6 vs 30.7 ms per
+// launch), while for the complex FP32 spectrum the register form wins
+// (15.6 vs 10.8 ms).
 bool epilogue_uses_warp(const SurveyDev& s, int num_sms) {
+  if (s.nt == 4096 && !field_in_nw(s)) return false;
   return s.ncols >= 16 * num_sms && epilogue_warp_supports(s.nt, s.nw);
 }
 

@@ -379,19 +379,23 @@ def _many_focal(n, nt, dt, F, fmax):
 @pytest.mark.parametrize("nt,dt,fmax,rprec", [(64, 0.016, None, 0), (128, 0.008, 40.0, 0), (256, 0.008, None, 0),
                                               (512, 0.004, 60.0, 0), (1024, 0.002, 90.0, 0), (2048, 0.001, 150.0, 0),
                                               (2048, 0.001, 150.0, 4), (512, 0.004, 60.0, 4), (1024, 0.002, 90.0, 1),
-                                              (256, 0.008, None, 2)])
+                                              (256, 0.008, None, 2), (4096, 0.0005, 200.0, 0),
+                                              (4096, 0.0005, 480.0, 4), (4096, 0.0005, 480.0, 5),
+                                              (4096, 0.0005, None, 0)])
 def test_register_epilogue_shapes(nt, dt, fmax, rprec):
     # enough traces (33 positions x 80 focal points) for the register epilogue
     # where the shape fits its shared memory (nt = 64, 512 with a narrow band,
-    # 1024, 2048; the others run the shared-memory epilogue): ragged blocks (33
-    # is no multiple of the block size), full and limited bands, and each output
-    # form (complex FP32 field spectrum; the 2- and 3-part 16-bit embeddings,
-    # BF16 and FP16), per iteration
+    # 1024, 2048, and 4096 with two warps per trace up to 984 bins for the
+    # complex FP32 spectrum; the others run the shared-memory epilogue):
+    # ragged blocks (33 is no multiple of the block size), full and limited
+    # bands, and each output form (complex FP32 field spectrum, also quantised
+    # by the scaled FP16 split; the 2- and 3-part 16-bit embeddings, BF16 and
+    # FP16), per iteration
     from tests.test_gpu_tensor import dequantised
     from paper_2106_04649_gb300.api import Plan
     s = _many_focal(33, nt, dt, 80, fmax)
     R, td, Gd = survey_inputs(s)
-    Rref = R.astype(np.complex128) if rprec in (0, 4) else dequantised(R, rprec)
+    Rref = R.astype(np.complex128) if rprec in (0, 4, 5) else dequantised(R, rprec)
     _, hist = M.run(Rref, Gd.astype(np.float64), td, s.eps, s.dt, s.dx, 3, history=True)
     p = Plan([desc_for(s, rprec=rprec)])
     p.load_R(0, R)
@@ -421,3 +425,50 @@ def test_few_focal_points_complex_fp32(n, F):
         _compare(p.fetch_fields(0), hist[i], TOL_ITER, TOL_N, f"n={n} F={F} iter {i}")
         assert np.max(np.abs(e[0] - hist[i].energy[i]) / hist[i].energy[i]) <= TOL_E
     p.close()
+
+
+@pytest.mark.parametrize("nt,dt,fmax,F,rprec", [(2048, 0.001, 150.0, 80, 4), (4096, 0.004, 60.0, 80, 0),
+                                                (4096, 0.0005, 480.0, 80, 5), (128, 0.008, 40.0, 3, 0)])
+def test_fetch_mid_series(nt, dt, fmax, F, rprec):
+    # Reading N, f1plus and f1min mid-series leaves the series untouched, bit
+    # for bit.  Fields that need a synthesis (f2p with pmin, G, G^- and G^+)
+    # overwrite the contraction's operand, which is then restored from N_last
+    # through the shared-memory transform, and a plan resumed from fetched N,
+    # f1plus and f1min starts from that transform too: both continue the
+    # series to FP32 rounding (register epilogue at nt = 2048 and 4096, whose
+    # own transform rounds differently, and the shared-memory epilogue).
+    from paper_2106_04649_gb300 import _native as N
+    from paper_2106_04649_gb300.api import Plan
+    s = _many_focal(33, nt, dt, F, fmax)
+    R, td, Gd = survey_inputs(s)
+    state = N.MK_F_N | N.MK_F_F1P | N.MK_F_F1M
+
+    def plan():
+        p = Plan([desc_for(s, rprec=rprec)])
+        p.load_R(0, R)
+        p.set_Gd_window(0, Gd, td, s.eps)
+        return p
+
+    def series(fetch_at=(), mask=N.MK_F_ALL):
+        p = plan()
+        for i in range(6):
+            p.iterate(1)
+            if i in fetch_at:
+                p.fetch_fields(0, mask)
+        out = p.fetch_fields(0)
+        p.close()
+        return out
+
+    plain = series()
+    assert np.array_equal(series(fetch_at=(1, 3), mask=state), plain)
+    assert rel_l2(series(fetch_at=(1, 3)), plain) <= 1e-6
+    p = plan()
+    p.iterate(3)
+    fields = p.fetch_fields(0, state)
+    p.close()
+    q = plan()
+    q.set_fields(0, np.ascontiguousarray(fields), 3, state)
+    q.iterate(3)
+    resumed = q.fetch_fields(0)
+    q.close()
+    assert rel_l2(resumed, plain) <= 1e-6
